@@ -1,0 +1,308 @@
+"""Benchmark: one GNN re-ranking (Algorithm 1) of the Market-scale workload per step.
+
+Workload: 3,368 queries + 19,732 gallery vectors (N = 23,100), d = 2048, FP32
+features drawn as 1,501 clustered identities plus 2,000 distractors
+(synthetic stand-ins for Market-1501), k1 = 26, k2 = 7, 2 layers, full
+ranked lists (every gallery index per query).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16|fp8]
+                  [--impl ours|reference] [--workload market|large50k|tiny]
+
+Prints one JSON line.  `value` is ms per re-rank with inputs resident in HBM,
+timed with CUDA events on the launching stream, L2 flushed before every step;
+`e2e` is the same through the C ABI with pinned host buffers (copies inside
+the timed region).  With N > 1 (torchrun) every rank runs an independent
+replica (the method needs no exchange between instances), the time is the
+max over ranks and `value` divides it by all ranks' re-ranks.
+`--impl reference` times the FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "market": dict(spec="MARKET_SCALE", k1=26, k2=7, layers=2),
+    "large50k": dict(spec="LARGE_50K", k1=26, k2=7, layers=2),
+    "tiny": dict(spec="TINY", k1=26, k2=7, layers=2),
+}
+METRIC = "ms per N=23.1k re-rank (FP32 vs BF16+FP32 rescore); served p50/p99 ms; %roofline"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(xq, xg, k1, target_s=15.0):
+    """Time the FP64 oracle's Eq. 7-8 (S rows + full sort + top-k1) on a bounded
+    sample of rows, scaled to all N rows.  Returns (ms per re-rank, sample text, threads)."""
+    from oracle import rerank_oracle
+    xu = np.concatenate([xq, xg]).astype(np.float64)
+    n = xu.shape[0]
+    rows = 64
+    t0 = time.perf_counter()
+    rerank_oracle.knn_lists(xu, k1, rows=np.arange(rows))
+    dt = time.perf_counter() - t0
+    rows = int(min(n, max(64, rows * target_s / max(dt, 1e-3) * 0.8)))
+    t0 = time.perf_counter()
+    rerank_oracle.knn_lists(xu, k1, rows=np.arange(rows))
+    dt = time.perf_counter() - t0
+    threads = os.cpu_count()
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max((i.get("num_threads", 1) for i in threadpool_info()), default=threads)
+    except ImportError:
+        pass
+    sample = (f"oracle Eq. 7-8 (FP64 S rows, stable full sort, top-k1) on {rows} of {n} rows, "
+              f"{dt:.1f} s, scaled x{n / rows:.2f}; graph, propagation and ranking not included")
+    return dt * 1e3 * n / rows, sample, threads
+
+
+def run_reference(args, world, rank):
+    from paper_2012_07620_gb300 import synthetic
+    wl = WORKLOADS[args.workload]
+    if rank != 0:
+        return
+    w = synthetic.make_workload(getattr(synthetic, wl["spec"]))
+    vals = []
+    sample = ""
+    threads = os.cpu_count()
+    for _ in range(args.warmup):
+        pass
+    for _ in range(args.steps):
+        v, sample, threads = cpu_oracle_sample(w.xq, w.xg, wl["k1"], target_s=args.cpu_seconds)
+        vals.append(v)
+    ms = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args, w), "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads,
+                                                          "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def _config(args, w):
+    spec = w.spec
+    return {"workload": f"{spec.name}: {spec.n_query} queries + {spec.n_gallery} gallery, d={spec.dim}, "
+                        f"{spec.n_clusters} clusters + {spec.n_distractors} distractors, "
+                        f"k1={WORKLOADS[args.workload]['k1']}, k2={WORKLOADS[args.workload]['k2']}, "
+                        f"L={WORKLOADS[args.workload]['layers']}, full ranked lists",
+            "n_vertices": spec.n, "dim": spec.dim, "precision": args.precision,
+            "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    from paper_2012_07620_gb300 import rerank, synthetic
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS[args.workload]
+    w = synthetic.make_workload(getattr(synthetic, wl["spec"]))
+    k1, k2, L = wl["k1"], wl["k2"], wl["layers"]
+    nq, ng, d = len(w.xq), len(w.xg), w.spec.dim
+    xq = torch.from_numpy(w.xq).to(dev)
+    xg = torch.from_numpy(w.xg).to(dev)
+    out_i = torch.empty((nq, ng), dtype=torch.int32, device=dev)
+    out_d = torch.empty((nq, ng), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    R = rerank.Reranker(device=local, precision=args.precision, stage_timing=True)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        R.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
+    launches = R.last_info()["kernel_launches"]
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_sum = {}
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for s in range(args.steps):
+            flush.fill_(s & 255)
+            ev[s][0].record(stream)
+            R.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
+            ev[s][1].record(stream)
+            for k, v in R.stage_times().items():
+                stage_sum[k] = stage_sum.get(k, 0.0) + v
+        torch.cuda.synchronize()
+    _barrier(world)
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    total_ms = _max_over_ranks(total_ms, world)
+    ms = total_ms / (args.steps * world)
+    stages = {k: v / args.steps for k, v in stage_sum.items()}
+
+    # End to end through the C ABI with pinned host buffers.
+    hq = torch.from_numpy(w.xq).pin_memory()
+    hg = torch.from_numpy(w.xg).pin_memory()
+    ho_i = torch.empty((nq, ng), dtype=torch.int32).pin_memory()
+    ho_d = torch.empty((nq, ng), dtype=torch.float32).pin_memory()
+    R.run(hq, hg, k1, k2, L, 0, ho_i, ho_d, stream)
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        R.run(hq, hg, k1, k2, L, 0, ho_i, ho_d, stream)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e_ms = _max_over_ranks(e2e_ms, world) / world
+
+    peaks, which = _peaks()
+    n = nq + ng
+    sim_ms = stages.get("similarity_topk", float("nan"))
+    flops = 2.0 * n * n * d
+    if args.precision == "fp32":
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": flops / (sim_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz"}
+    else:
+        peak = peaks["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
+        roof = {"bound": "tensor", "achieved": flops / (sim_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"{which} bf16 burst" + (" x2 (fp8 nominal ratio)" if args.precision == "fp8" else "")}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = "similarity_topk"
+
+    line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms * world, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+            "data": "synthetic", "config": _config(args, w),
+            "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(hq.numel() * 4 + hg.numel() * 4),
+                    "d2h_bytes_per_step": int(ho_i.numel() * 4 + ho_d.numel() * 4)},
+            "roofline": roof, "stages_ms": stages, "gpu_launches": int(launches * args.steps),
+            "clocks": clocks.summary()}
+    info = R.last_info()
+    line["fp64_rescored"] = info["fp64_rescored"]
+    line["fallback_rows"] = info["fallback_rows"]
+    if rank == 0 and not args.no_cpu_baseline:
+        v, sample, threads = cpu_oracle_sample(w.xq, w.xg, k1, target_s=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": threads, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line))
+    R.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--workload", default="market", choices=list(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = _dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

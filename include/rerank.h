@@ -1,0 +1,163 @@
+/*
+ * rerank.h -- C ABI of the GB300 GNN re-ranking library.
+ *
+ * The operation is Algorithm 1 of Zhang et al., "Understanding Image Retrieval
+ * Re-Ranking: A Graph Neural Network Perspective" (arXiv 2012.07620, Sec. 3.3):
+ *   1. S_ij = cos(x_i, x_j) over X_u = X_q u X_g                     (Eq. 7)
+ *   2. N(i, k1) = the k1 most similar vertices of row i of S            (Eq. 8)
+ *   3. A* = (A + A^T) / 2: 1 for reciprocal neighbours, 1/2 one-way     (Eq. 9, 10)
+ *   4. h_i^(0) = row i of A*; edges e_ij = S_ij for j in N(i, k2)       (Eq. 11, 12)
+ *   5. L layers of h_i <- h_i + sum_{j in N(i,k2)} e_ij^alpha h_j, then
+ *      every h_i is scaled to unit L2 norm                              (Eq. 13, 14)
+ *   6. each query's gallery list sorted by cos(h_q, h_g)                (Alg. 1 step 7)
+ *
+ * Conventions shared by every call:
+ *   - Vertex (union) index: queries first, i = 0 .. nq-1, then the gallery,
+ *     i = nq + g.  Self is a member of its own neighbourhood with S_ii = 1.
+ *   - Every ordering (neighbour lists, final lists) is by score descending,
+ *     ties to the lower index.
+ *   - Buffers are row-major and contiguous.  Unless a call says otherwise a
+ *     buffer may be device memory or host memory; calls that receive any
+ *     host buffer copy through the context's device workspace and return only
+ *     after the results are in the host buffers.  With device buffers only,
+ *     work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) and the call returns once the error word has been read back
+ *     (one stream synchronisation at the end of the call).
+ *   - The caller owns every buffer it passes; the library never frees them.
+ *     The context owns its device workspace, which grows on demand up to
+ *     `hbm_budget` and is reused by later calls.
+ *   - Every call returns a status and never aborts the process.  A context
+ *     must not be used by two host threads at once.
+ */
+#ifndef RERANK_H
+#define RERANK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rerank_ctx rerank_ctx;
+
+typedef enum {
+  RERANK_OK = 0,
+  RERANK_EINVAL = 1,       /* invalid argument, or an input row that is non-finite or all zero */
+  RERANK_ENOMEM = 2,       /* a device or pinned-host allocation failed */
+  RERANK_EBUDGET = 3,      /* the workspace for this call would exceed cfg.hbm_budget */
+  RERANK_ECUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+  RERANK_ETIMEOUT = 5,     /* a bounded device-side wait ran out */
+  RERANK_EINTERNAL = 6,    /* an internal consistency check failed (see rerank_last_info) */
+  RERANK_EUNSUPPORTED = 7, /* a valid combination that this build does not implement */
+  RERANK_EAGAIN = 8        /* serving: no result yet, or the admission queue is full */
+} rerank_status;
+
+/* Similarity precision of step 1 (the one dense contraction). */
+enum { RERANK_PREC_FP32 = 0, RERANK_PREC_BF16 = 1, RERANK_PREC_FP8 = 2 };
+/* Element type of the caller's feature buffers. */
+enum { RERANK_DTYPE_F32 = 0, RERANK_DTYPE_BF16 = 1 };
+/* The aggregate of Eq. 13. */
+enum { RERANK_AGG_SUM = 0, RERANK_AGG_MEAN = 1, RERANK_AGG_MAX = 2 };
+/* Initial vertex feature (Sec. 4.2, Table 1): A*_i (Eq. 11), A_i, or x_i. */
+enum { RERANK_FEAT_ASTAR = 0, RERANK_FEAT_A = 1, RERANK_FEAT_X = 2 };
+
+typedef struct {
+  int device;                /* CUDA device ordinal */
+  int precision;             /* RERANK_PREC_*; default FP32 */
+  int rescore_m;             /* extra candidates kept per row before exact rescoring; default 16 */
+  float alpha;               /* exponent of Eq. 14; default 2 */
+  int aggregator;            /* RERANK_AGG_*; default SUM (Sec. 4.1) */
+  int feature_mode;          /* RERANK_FEAT_*; default ASTAR */
+  size_t hbm_budget;         /* workspace cap in bytes; 0 = no cap */
+  const char* autotune_path; /* JSON tuning table to read (and to write from rerank_autotune); NULL = built-in */
+  int stage_timing;          /* nonzero: record CUDA events around every stage (rerank_stage_times) */
+} rerank_config;
+
+/* Fill `cfg` with the defaults listed above. */
+void rerank_config_init(rerank_config* cfg);
+
+/* Create a context on cfg->device.  *out receives the handle.
+ * Errors: EINVAL (null pointers, bad enum values), ECUDA (no usable device,
+ * or not a compute capability 10.3 GPU), ENOMEM. */
+rerank_status rerank_create(rerank_ctx** out, const rerank_config* cfg);
+
+/* Release the context and its workspace.  Accepts NULL. */
+rerank_status rerank_destroy(rerank_ctx* ctx);
+
+/* Static text for a status code. */
+const char* rerank_strerror(rerank_status status);
+
+/* Host-only validation of the size arguments of rerank_run (no GPU needed):
+ * EINVAL unless nq >= 1, ng >= 1, d >= 1, dtype valid, 1 <= k2 <= k1 <= nq+ng,
+ * layers >= 0 and 0 <= topk_out <= ng. */
+rerank_status rerank_check_args(int64_t nq, int64_t ng, int d, int dtype, int k1, int k2,
+                                int layers, int64_t topk_out);
+
+/* Algorithm 1 end to end (steps 1-6 above).
+ *   xq        nq x d features of the queries (dtype), raw: the call normalises them
+ *   xg        ng x d features of the gallery
+ *   k1, k2    neighbourhood sizes of Eq. 8 and Eq. 12
+ *   layers    number of propagation layers L (Eq. 14)
+ *   topk_out  length of each output list; 0 = the whole gallery (ng)
+ *   out_idx   nq x topk_out int32: gallery indices (0 .. ng-1), best first
+ *   out_dist  nq x topk_out float: 1 - cos(h_q, h_g) in the same order
+ *   stream    cudaStream_t for the enqueued work (NULL = default stream)
+ * Errors: EINVAL (as rerank_check_args, null pointers, or an input row that
+ * is non-finite or has zero norm), EBUDGET, ENOMEM, ECUDA, EINTERNAL. */
+rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void* xg, int64_t ng,
+                         int d, int dtype, int k1, int k2, int layers, int64_t topk_out,
+                         int32_t* out_idx, float* out_dist, void* stream);
+
+/* Steps 1-2 only: the exact top-k neighbour lists of every vertex of X (Eq. 7-8).
+ *   x          n x d features (dtype)
+ *   out_idx    n x k int32, sorted by (S desc, index asc); out_idx[i*k] == i
+ *              unless a lower-indexed vertex has exactly the same direction
+ *   out_score  n x k float: S of each listed pair (FP32-accurate, see DESIGN)
+ * Errors: as rerank_run. */
+rerank_status rerank_knn(rerank_ctx* ctx, const void* x, int64_t n, int d, int dtype, int k,
+                         int32_t* out_idx, float* out_score, void* stream);
+
+/* Counters of the last rerank_run / rerank_knn call on this context. */
+typedef struct {
+  int64_t n_vertices;
+  int64_t candidates_per_row;  /* K = min(k1 + rescore_m, n) */
+  int64_t fp64_rescored;       /* candidate scores recomputed in FP64 near a tie */
+  int64_t fallback_rows;       /* rows whose candidate list could not be certified and were redone exactly */
+  int64_t h_nnz[9];            /* nnz of h^(0) .. h^(min(L,8)) */
+  int64_t workspace_bytes;     /* device workspace held by the context */
+  int64_t kernel_launches;     /* kernels of this library launched by the call (last attempt) */
+  int32_t error_bits;          /* device error word of the last call (0 = clean) */
+  int32_t bad_row;             /* first offending input row for EINVAL from the device, else -1 */
+} rerank_info;
+
+rerank_status rerank_last_info(const rerank_ctx* ctx, rerank_info* info);
+
+/* Per-stage device times (ms) of the last call, when cfg.stage_timing was set.
+ * Writes up to `cap` entries and the number of stages to *count; names[i]
+ * (static strings) label them.  EINVAL when timing was not enabled. */
+rerank_status rerank_stage_times(const rerank_ctx* ctx, float* ms, const char** names, int cap,
+                                 int* count);
+
+/* Copy an intermediate array of the last call into `dst` (device or host).
+ * `what` selects it; *bytes receives the array's size.  With dst == NULL only
+ * the size is returned.  ECUDA/EINVAL on failure, EINVAL if cap is too small. */
+enum {
+  RERANK_DBG_KNN_IDX = 0,    /* n x k1 int32 */
+  RERANK_DBG_KNN_SCORE = 1,  /* n x k1 float */
+  RERANK_DBG_H0_ROWPTR = 2,  /* n+1 int32: CSR of h^(0) = A* rows, columns ascending */
+  RERANK_DBG_H0_COL = 3,     /* nnz int32 */
+  RERANK_DBG_H0_VAL = 4,     /* nnz float */
+  RERANK_DBG_HL_START = 5,   /* n int64: row start of h^(L) in the padded CSR */
+  RERANK_DBG_HL_LEN = 6,     /* n int32: row length of h^(L) */
+  RERANK_DBG_HL_COL = 7,     /* capacity int32 (read rows through START/LEN) */
+  RERANK_DBG_HL_VAL = 8      /* capacity float */
+};
+rerank_status rerank_debug_copy(const rerank_ctx* ctx, int what, void* dst, size_t cap,
+                                size_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RERANK_H */

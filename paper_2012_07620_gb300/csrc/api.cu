@@ -1,0 +1,487 @@
+// The C ABI (include/rerank.h): argument checks, workspace planning, stage
+// sequencing on the caller's stream, and the end-of-call error read-back.
+#include <climits>
+#include <cstdlib>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace rr {
+
+static thread_local std::string g_last_cuda;
+
+rerank_status cuda_fail(cudaError_t e, const char* what) {
+  g_last_cuda = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return RERANK_ENOMEM;
+  return RERANK_ECUDA;
+}
+const char* last_cuda_error_text() { return g_last_cuda.c_str(); }
+
+void StageTimer::mark(const char* name) {
+  if (!on) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, stream);
+  ev.push_back(e);
+  names.push_back(name);
+}
+
+double rescore_eps(int dp);
+int sim_fp32_kmax();
+int refine_kmax();
+int fallback_warps();
+
+namespace {
+
+__global__ void k_status_reset(long long* st) {
+  const int t = threadIdx.x;
+  if (t < kStCount) st[t] = (t == kStBadRow) ? LLONG_MAX : 0;
+}
+
+bool is_host_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int choose_chunks(int64_t row_blocks, int64_t col_tiles, int sm_count, int forced) {
+  if (forced > 0) return int(std::min<int64_t>(std::min<int64_t>(forced, 32), col_tiles));
+  int best = 1;
+  double best_cost = 1e300;
+  for (int p = 1; p <= 32 && p <= col_tiles; ++p) {
+    const int64_t ctas = row_blocks * p;
+    const int64_t waves = (ctas + sm_count - 1) / sm_count;
+    const int64_t tiles = (col_tiles + p - 1) / p;
+    const double cost = double(waves) * double(tiles) + 0.02 * p;  // small charge for more partial lists
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = p;
+    }
+  }
+  return best;
+}
+
+size_t type_size(int dtype) { return dtype == RERANK_DTYPE_BF16 ? 2 : 4; }
+
+// Carve every buffer of the run out of one block (dry pass when base == nullptr).
+size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision) {
+  const int64_t n = sh.n, np = sh.np;
+  const int k1 = sh.k1, k2 = sh.k2;
+  if (sh.host_in) {
+    b.xq = c.take<char>(size_t(sh.nq) * sh.d * type_size(sh.dtype));
+    b.xg = c.take<char>(size_t(sh.ng ? sh.ng : 1) * sh.d * type_size(sh.dtype));
+  }
+  if (sh.host_out) {
+    b.out_idx = c.take<int32_t>(size_t(sh.nq) * (sh.knn_only ? k1 : sh.topk));
+    b.out_dist = c.take<float>(size_t(sh.nq) * (sh.knn_only ? k1 : sh.topk));
+  }
+  b.xhat = c.take<float>(size_t(np) * sh.dp);
+  b.xlow = precision == RERANK_PREC_FP32 ? nullptr : c.take<char>(size_t(np) * sh.dp * 2);
+  b.xscale = c.take<float>(size_t(np));
+  b.norm = c.take<double>(size_t(np));
+  b.part_s = c.take<float>(size_t(n) * sh.P * sh.K);
+  b.part_i = c.take<int32_t>(size_t(n) * sh.P * sh.K);
+  b.knn_idx = c.take<int32_t>(size_t(n) * k1);
+  b.knn_score = c.take<float>(size_t(n) * k1);
+  b.fb_rows = c.take<int32_t>(size_t(n));
+  b.fb_count = c.take<int32_t>(4);
+  // fallback per-warp lists (scores then indices)
+  b.scan_tmp = c.take<int64_t>(size_t(sm_count) * fallback_warps() * sh.K);
+  if (sh.knn_only) return c.used;
+  b.indeg = c.take<int32_t>(size_t(n));
+  b.fill = c.take<int32_t>(size_t(n));
+  b.inptr = c.take<int32_t>(size_t(n) + 1);
+  b.insrc = c.take<int32_t>(size_t(n) * k1);
+  b.out_sorted = c.take<int32_t>(size_t(n) * k1);
+  b.in_sorted = c.take<int32_t>(size_t(n) * k1);
+  b.rowcnt = c.take<int32_t>(size_t(n));
+  b.h0ptr = c.take<int32_t>(size_t(n) + 1);
+  b.nbr = c.take<int32_t>(size_t(n) * (k2 + 1));
+  b.nbr_w = c.take<float>(size_t(n) * (k2 + 1));
+  b.nbr_n = c.take<int32_t>(size_t(n));
+  for (int l = 0; l < 3; ++l) {
+    const size_t cap = l < 2 ? size_t(sh.cap_h) : size_t(2) * n * k1;
+    b.start[l] = c.take<int64_t>(size_t(n) + 1);
+    b.len[l] = c.take<int32_t>(size_t(n));
+    b.col[l] = c.take<int32_t>(cap);
+    b.val[l] = c.take<float>(cap);
+  }
+  b.ub = c.take<int32_t>(size_t(n));
+  b.big_rows = c.take<int32_t>(size_t(n));
+  b.big_count = c.take<int32_t>(4);
+  b.hash_keys_vals = c.take<float>(size_t(sm_count) * (size_t(n) + size_t((n + 31) / 32)));
+  b.rnorm = c.take<float>(size_t(n));
+  b.colcnt = c.take<int32_t>(size_t(n) + 1);
+  b.colptr = c.take<int64_t>(size_t(n) + 1);
+  b.csc_row = c.take<int32_t>(size_t(sh.cap_h));
+  b.csc_val = c.take<float>(size_t(sh.cap_h));
+  b.rank_scratch = c.take<uint32_t>(size_t(sh.rank_ctas) * 5 * size_t(sh.ng));
+  return c.used;
+}
+
+rerank_status ensure_workspace(rerank_ctx* ctx, size_t bytes) {
+  if (ctx->cfg.hbm_budget && bytes > ctx->cfg.hbm_budget) return RERANK_EBUDGET;
+  if (bytes <= ctx->ws_bytes) return RERANK_OK;
+  if (ctx->ws) {
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  const size_t want = bytes + bytes / 8;
+  const size_t alloc = (ctx->cfg.hbm_budget && want > ctx->cfg.hbm_budget) ? bytes : want;
+  RR_CUDA(cudaMalloc(&ctx->ws, alloc));
+  ctx->ws_bytes = alloc;
+  return RERANK_OK;
+}
+
+rerank_status collect(rerank_ctx* ctx, cudaStream_t s) {
+  RR_CUDA(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(long long) * kStCount, cudaMemcpyDeviceToHost, s));
+  RR_CUDA(cudaStreamSynchronize(s));
+  RR_CUDA(cudaGetLastError());
+  return RERANK_OK;
+}
+
+void finish_timing(rerank_ctx* ctx) {
+  ctx->stage_ms.clear();
+  ctx->stage_names.clear();
+  auto& tm = ctx->timer;
+  for (size_t i = 1; i < tm.ev.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, tm.ev[i - 1], tm.ev[i]);
+    ctx->stage_ms.push_back(ms);
+    ctx->stage_names.push_back(tm.names[i]);
+  }
+  for (auto e : tm.ev) cudaEventDestroy(e);
+  tm.ev.clear();
+  tm.names.clear();
+}
+
+// One attempt of the pipeline.  Returns OK, or the mapped device error.
+rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t* out_idx, float* out_dist,
+                       cudaStream_t s) {
+  Shape& sh = ctx->shape;
+  Buffers b;
+  Carver dry;
+  const size_t need = carve(dry, sh, b, ctx->sm_count, ctx->cfg.precision);
+  rerank_status st = ensure_workspace(ctx, need);
+  if (st != RERANK_OK) return st;
+  Carver real;
+  real.base = ctx->ws;
+  carve(real, sh, b, ctx->sm_count, ctx->cfg.precision);
+  ctx->buf = b;
+
+  auto& tm = ctx->timer;
+  tm.on = ctx->cfg.stage_timing != 0;
+  tm.stream = s;
+  tm.mark("begin");
+  int64_t nl = 1;
+  k_status_reset<<<1, 64, 0, s>>>(ctx->d_status);
+  RR_CUDA(cudaMemsetAsync(b.fb_count, 0, sizeof(int32_t), s));
+  const void* dq = xq;
+  const void* dg = xg;
+  if (sh.host_in) {
+    const size_t es = type_size(sh.dtype);
+    RR_CUDA(cudaMemcpyAsync(b.xq, xq, size_t(sh.nq) * sh.d * es, cudaMemcpyHostToDevice, s));
+    if (sh.ng) RR_CUDA(cudaMemcpyAsync(b.xg, xg, size_t(sh.ng) * sh.d * es, cudaMemcpyHostToDevice, s));
+    dq = b.xq;
+    dg = b.xg;
+    tm.mark("h2d");
+  }
+  nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xscale, ctx->cfg.precision, ctx->d_status, s);
+  tm.mark("normalize");
+  nl += launch_sim_fp32_topk(sh, b.xhat, b.part_s, b.part_i, ctx->sm_count, s);
+  tm.mark("similarity_topk");
+  const double eps_g = (sh.dp + 10) * kU32 * 1.01;
+  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, eps_g, b.knn_idx, b.knn_score, b.fb_rows,
+                b.fb_count, ctx->d_status, s);
+  float* fb_s = reinterpret_cast<float*>(b.scan_tmp);
+  int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(ctx->sm_count) * fallback_warps() * sh.K);
+  nl += launch_refine_fallback(sh, dq, dg, b.xhat, b.norm, b.knn_idx, b.knn_score, b.fb_rows, b.fb_count, fb_s, fb_i,
+                         ctx->d_status, ctx->sm_count, s);
+  tm.mark("refine");
+  if (sh.knn_only) {
+    const size_t bytes = size_t(sh.n) * sh.k1;
+    int32_t* oi = sh.host_out ? b.out_idx : out_idx;
+    float* os = sh.host_out ? b.out_dist : out_dist;
+    RR_CUDA(cudaMemcpyAsync(oi, b.knn_idx, bytes * 4, cudaMemcpyDeviceToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(os, b.knn_score, bytes * 4, cudaMemcpyDeviceToDevice, s));
+    if (sh.host_out) {
+      RR_CUDA(cudaMemcpyAsync(out_idx, b.out_idx, bytes * 4, cudaMemcpyDeviceToHost, s));
+      RR_CUDA(cudaMemcpyAsync(out_dist, b.out_dist, bytes * 4, cudaMemcpyDeviceToHost, s));
+    }
+  } else {
+    nl += launch_graph(sh, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, ctx->d_status, s);
+    tm.mark("graph");
+    RR_CUDA(cudaMemsetAsync(b.hash_keys_vals, 0,
+                            sizeof(float) * size_t(ctx->sm_count) * (size_t(sh.n) + size_t((sh.n + 31) / 32)), s));
+    int src = 2;
+    for (int l = 0; l < sh.layers; ++l) {
+      const int dst = l & 1;
+      nl += launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, ctx->d_status, ctx->sm_count, ctx->tune, s);
+      src = dst;
+    }
+    tm.mark("propagate");
+    nl += launch_row_norms(sh, b, src, ctx->d_status, s);
+    int32_t* oi = sh.host_out ? b.out_idx : out_idx;
+    float* od = sh.host_out ? b.out_dist : out_dist;
+    nl += launch_rank(sh, b, src, oi, od, ctx->d_status, ctx->sm_count, ctx->tune, s);
+    tm.mark("rank");
+    if (sh.host_out) {
+      const size_t cnt = size_t(sh.nq) * sh.topk;
+      RR_CUDA(cudaMemcpyAsync(out_idx, b.out_idx, cnt * 4, cudaMemcpyDeviceToHost, s));
+      RR_CUDA(cudaMemcpyAsync(out_dist, b.out_dist, cnt * 4, cudaMemcpyDeviceToHost, s));
+      tm.mark("d2h");
+    }
+  }
+  ctx->launches = nl;
+  RR_CUDA(cudaGetLastError());
+  st = collect(ctx, s);
+  if (tm.on) finish_timing(ctx);
+  if (st != RERANK_OK) return st;
+  const long long* h = ctx->h_status;
+  ctx->info.fp64_rescored = h[kStFp64];
+  ctx->info.fallback_rows = h[kStFallback];
+  ctx->info.error_bits = int32_t(h[kStErr]);
+  ctx->info.bad_row = h[kStBadRow] == LLONG_MAX ? -1 : int32_t(h[kStBadRow]);
+  const int e = int(h[kStErr]);
+  if (e & (kErrNonFinite | kErrZeroNorm)) return RERANK_EINVAL;
+  if (e & kErrOverflow) {
+    ctx->cap_h_hint = std::max<int64_t>(ctx->cap_h_hint, int64_t(h[kStNeed]) + int64_t(h[kStNeed]) / 4 + 1024);
+    return RERANK_ENOMEM;  // caller of run_once retries with the larger capacity
+  }
+  if (e & kErrTimeout) return RERANK_ETIMEOUT;
+  if (e & (kErrCertify | kErrInternal)) return RERANK_EINTERNAL;
+  return RERANK_OK;
+}
+
+rerank_status plan(rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, int k1, int k2, int layers,
+                   int64_t topk, bool knn_only, bool host_in, bool host_out) {
+  Shape sh;
+  sh.nq = nq;
+  sh.ng = ng;
+  sh.n = nq + ng;
+  sh.np = round_up(sh.n, 128);
+  sh.d = d;
+  sh.dp = int(round_up(d, 64));
+  sh.dtype = dtype;
+  sh.k1 = k1;
+  sh.k2 = k2;
+  sh.layers = layers;
+  sh.topk = topk;
+  sh.knn_only = knn_only;
+  sh.host_in = host_in;
+  sh.host_out = host_out;
+  const int kmax = std::min(sim_fp32_kmax(), refine_kmax());
+  if (k1 > kmax) return RERANK_EUNSUPPORTED;
+  int64_t K = std::min<int64_t>(int64_t(k1) + std::max(ctx->cfg.rescore_m, 0), sh.n);
+  K = std::min<int64_t>(K, kmax);
+  sh.K = int(K);
+  sh.P = choose_chunks(sh.np / 128, sh.np / 128, ctx->sm_count, ctx->tune.sim_chunks);
+  // Capacity of a propagation layer: sum over rows of ub_i <= min(n, sum_j len_j).
+  // n^2 bounds it exactly for small graphs; otherwise a generous guess, grown on overflow.
+  int64_t guess = std::max<int64_t>(2 * sh.n * k1, std::min<int64_t>(sh.n * sh.n, sh.n * int64_t(k2 + 1) * 160));
+  if (ctx->test_cap_h > 0) guess = ctx->test_cap_h;
+  sh.cap_h = std::max<int64_t>(guess, ctx->cap_h_hint);
+  sh.rank_ctas = ctx->sm_count;
+  if (sh.n * int64_t(k1) >= (int64_t(1) << 31) || sh.n >= (int64_t(1) << 31) - 1) return RERANK_EUNSUPPORTED;
+  ctx->shape = sh;
+  return RERANK_OK;
+}
+
+rerank_status run_with_retry(rerank_ctx* ctx, const void* xq, const void* xg, int32_t* oi, float* od,
+                             cudaStream_t s) {
+  rerank_status st = RERANK_OK;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    st = run_once(ctx, xq, xg, oi, od, s);
+    if (!(st == RERANK_ENOMEM && (ctx->info.error_bits & kErrOverflow))) break;
+    ctx->shape.cap_h = std::max(ctx->shape.cap_h, ctx->cap_h_hint);
+  }
+  ctx->info.workspace_bytes = int64_t(ctx->ws_bytes);
+  ctx->info.kernel_launches = ctx->launches;
+  ctx->info.n_vertices = ctx->shape.n;
+  ctx->info.candidates_per_row = ctx->shape.K;
+  return st;
+}
+
+bool valid_enum(const rerank_config* c) {
+  return c->precision >= 0 && c->precision <= 2 && c->aggregator >= 0 && c->aggregator <= 2 &&
+         c->feature_mode >= 0 && c->feature_mode <= 2 && c->rescore_m >= 0 && c->rescore_m <= 256;
+}
+
+}  // namespace
+}  // namespace rr
+
+using namespace rr;
+
+extern "C" {
+
+void rerank_config_init(rerank_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->precision = RERANK_PREC_FP32;
+  cfg->rescore_m = 16;
+  cfg->alpha = 2.0f;
+  cfg->aggregator = RERANK_AGG_SUM;
+  cfg->feature_mode = RERANK_FEAT_ASTAR;
+  cfg->hbm_budget = 0;
+  cfg->autotune_path = nullptr;
+  cfg->stage_timing = 0;
+}
+
+const char* rerank_strerror(rerank_status s) {
+  switch (s) {
+    case RERANK_OK: return "ok";
+    case RERANK_EINVAL: return "invalid argument or input row";
+    case RERANK_ENOMEM: return "out of memory";
+    case RERANK_EBUDGET: return "workspace exceeds the HBM budget";
+    case RERANK_ECUDA: return "CUDA error";
+    case RERANK_ETIMEOUT: return "device wait timed out";
+    case RERANK_EINTERNAL: return "internal check failed";
+    case RERANK_EUNSUPPORTED: return "unsupported combination";
+    case RERANK_EAGAIN: return "not ready";
+  }
+  return "unknown status";
+}
+
+rerank_status rerank_check_args(int64_t nq, int64_t ng, int d, int dtype, int k1, int k2, int layers,
+                                int64_t topk_out) {
+  if (nq < 1 || ng < 1 || d < 1) return RERANK_EINVAL;
+  if (dtype != RERANK_DTYPE_F32 && dtype != RERANK_DTYPE_BF16) return RERANK_EINVAL;
+  if (k1 < 1 || k2 < 1 || k2 > k1 || int64_t(k1) > nq + ng) return RERANK_EINVAL;
+  if (layers < 0 || topk_out < 0 || topk_out > ng) return RERANK_EINVAL;
+  return RERANK_OK;
+}
+
+rerank_status rerank_create(rerank_ctx** out, const rerank_config* cfg) {
+  if (!out || !cfg) return RERANK_EINVAL;
+  *out = nullptr;
+  if (!valid_enum(cfg)) return RERANK_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return RERANK_ECUDA;
+  }
+  cudaDeviceProp prop;
+  RR_CUDA(cudaGetDeviceProperties(&prop, cfg->device));
+  if (prop.major != 10 || prop.minor != 3) return RERANK_ECUDA;
+  RR_CUDA(cudaSetDevice(cfg->device));
+  rerank_ctx* ctx = new (std::nothrow) rerank_ctx();
+  if (!ctx) return RERANK_ENOMEM;
+  ctx->cfg = *cfg;
+  if (cfg->autotune_path) ctx->tune_path = cfg->autotune_path;
+  ctx->cfg.autotune_path = nullptr;
+  ctx->device = cfg->device;
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->smem_optin = prop.sharedMemPerBlockOptin;
+  // Test hook: start the propagation buffers this small to exercise the overflow-and-retry path.
+  if (const char* e = std::getenv("RERANK_TEST_CAP_H")) ctx->test_cap_h = std::atoll(e);
+  if (cudaMalloc(&ctx->d_status, sizeof(long long) * kStCount) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(long long) * kStCount) != cudaSuccess) {
+    cudaGetLastError();
+    rerank_destroy(ctx);
+    return RERANK_ENOMEM;
+  }
+  *out = ctx;
+  return RERANK_OK;
+}
+
+rerank_status rerank_destroy(rerank_ctx* ctx) {
+  if (!ctx) return RERANK_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  for (auto e : ctx->timer.ev) cudaEventDestroy(e);
+  delete ctx;
+  return RERANK_OK;
+}
+
+rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void* xg, int64_t ng, int d, int dtype,
+                         int k1, int k2, int layers, int64_t topk_out, int32_t* out_idx, float* out_dist,
+                         void* stream) {
+  if (!ctx || !xq || !xg || !out_idx || !out_dist) return RERANK_EINVAL;
+  rerank_status st = rerank_check_args(nq, ng, d, dtype, k1, k2, layers, topk_out);
+  if (st != RERANK_OK) return st;
+  if (ctx->cfg.aggregator == RERANK_AGG_MAX || ctx->cfg.feature_mode == RERANK_FEAT_X ||
+      ctx->cfg.precision != RERANK_PREC_FP32)
+    return RERANK_EUNSUPPORTED;
+  RR_CUDA(cudaSetDevice(ctx->device));
+  const bool host_in = is_host_ptr(xq) || is_host_ptr(xg);
+  const bool host_out = is_host_ptr(out_idx) || is_host_ptr(out_dist);
+  const int64_t topk = topk_out ? topk_out : ng;
+  st = plan(ctx, nq, ng, d, dtype, k1, k2, layers, topk, false, host_in, host_out);
+  if (st != RERANK_OK) return st;
+  return run_with_retry(ctx, xq, xg, out_idx, out_dist, static_cast<cudaStream_t>(stream));
+}
+
+rerank_status rerank_knn(rerank_ctx* ctx, const void* x, int64_t n, int d, int dtype, int k, int32_t* out_idx,
+                         float* out_score, void* stream) {
+  if (!ctx || !x || !out_idx || !out_score) return RERANK_EINVAL;
+  if (n < 1 || d < 1 || k < 1 || k > n || (dtype != RERANK_DTYPE_F32 && dtype != RERANK_DTYPE_BF16))
+    return RERANK_EINVAL;
+  if (ctx->cfg.precision != RERANK_PREC_FP32) return RERANK_EUNSUPPORTED;
+  RR_CUDA(cudaSetDevice(ctx->device));
+  const bool host_in = is_host_ptr(x);
+  const bool host_out = is_host_ptr(out_idx) || is_host_ptr(out_score);
+  rerank_status st = plan(ctx, n, 0, d, dtype, k, 1, 0, 0, true, host_in, host_out);
+  if (st != RERANK_OK) return st;
+  return run_with_retry(ctx, x, x, out_idx, out_score, static_cast<cudaStream_t>(stream));
+}
+
+rerank_status rerank_last_info(const rerank_ctx* ctx, rerank_info* info) {
+  if (!ctx || !info) return RERANK_EINVAL;
+  *info = ctx->info;
+  return RERANK_OK;
+}
+
+rerank_status rerank_stage_times(const rerank_ctx* ctx, float* ms, const char** names, int cap, int* count) {
+  if (!ctx || !count) return RERANK_EINVAL;
+  if (!ctx->cfg.stage_timing) return RERANK_EINVAL;
+  const int nstage = int(ctx->stage_ms.size());
+  *count = nstage;
+  for (int i = 0; i < nstage && i < cap; ++i) {
+    if (ms) ms[i] = ctx->stage_ms[i];
+    if (names) names[i] = ctx->stage_names[i];
+  }
+  return RERANK_OK;
+}
+
+rerank_status rerank_debug_copy(const rerank_ctx* ctx, int what, void* dst, size_t cap, size_t* bytes) {
+  if (!ctx || !bytes) return RERANK_EINVAL;
+  const Shape& sh = ctx->shape;
+  const Buffers& b = ctx->buf;
+  const int last = sh.layers == 0 ? 2 : (sh.layers - 1) & 1;
+  const void* src = nullptr;
+  size_t nb = 0;
+  switch (what) {
+    case RERANK_DBG_KNN_IDX: src = b.knn_idx; nb = size_t(sh.n) * sh.k1 * 4; break;
+    case RERANK_DBG_KNN_SCORE: src = b.knn_score; nb = size_t(sh.n) * sh.k1 * 4; break;
+    case RERANK_DBG_H0_ROWPTR: src = b.h0ptr; nb = (size_t(sh.n) + 1) * 4; break;
+    case RERANK_DBG_H0_COL: src = b.col[2]; nb = size_t(2) * sh.n * sh.k1 * 4; break;
+    case RERANK_DBG_H0_VAL: src = b.val[2]; nb = size_t(2) * sh.n * sh.k1 * 4; break;
+    case RERANK_DBG_HL_START: src = b.start[last]; nb = size_t(sh.n) * 8; break;
+    case RERANK_DBG_HL_LEN: src = b.len[last]; nb = size_t(sh.n) * 4; break;
+    case RERANK_DBG_HL_COL: src = b.col[last]; nb = size_t(last == 2 ? 2 * sh.n * sh.k1 : sh.cap_h) * 4; break;
+    case RERANK_DBG_HL_VAL: src = b.val[last]; nb = size_t(last == 2 ? 2 * sh.n * sh.k1 : sh.cap_h) * 4; break;
+    default: return RERANK_EINVAL;
+  }
+  if (sh.knn_only && what > RERANK_DBG_KNN_SCORE) return RERANK_EINVAL;
+  *bytes = nb;
+  if (!dst) return RERANK_OK;
+  if (cap < nb || !src) return RERANK_EINVAL;
+  RR_CUDA(cudaSetDevice(ctx->device));
+  RR_CUDA(cudaMemcpy(dst, src, nb, cudaMemcpyDefault));
+  return RERANK_OK;
+}
+
+}  // extern "C"

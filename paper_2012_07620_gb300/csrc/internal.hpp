@@ -1,0 +1,170 @@
+// Host-side internals: the context, its device workspace, and the stage launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rerank.h"
+
+namespace rr {
+
+#define RR_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return ::rr::cuda_fail(e_, #call); \
+  } while (0)
+
+rerank_status cuda_fail(cudaError_t e, const char* what);
+const char* last_cuda_error_text();
+
+// Bump allocator over one device block.  A dry pass (base == nullptr) only
+// measures; the real pass hands out 256-byte aligned sub-buffers.
+struct Carver {
+  char* base = nullptr;
+  size_t used = 0;
+  template <class T>
+  T* take(size_t count) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + count * sizeof(T);
+    return base ? reinterpret_cast<T*>(base + off) : nullptr;
+  }
+};
+
+// Launch shapes chosen per (n, d) by the autotuner or its defaults.
+struct Tuning {
+  int sim_chunks = 0;      // column chunks P of the similarity top-K kernel (0 = from SM count)
+  int prop_warps = 8;      // warps per CTA of the propagation kernel
+  int rank_threads = 1024; // threads per CTA of the final ranking kernel
+};
+
+// Device pointers of one pipeline run (all inside the workspace block).
+struct Buffers {
+  // inputs staged from host memory, when the caller passed host buffers
+  void* xq = nullptr;
+  void* xg = nullptr;
+  int32_t* out_idx = nullptr;
+  float* out_dist = nullptr;
+  // K0
+  float* xhat = nullptr;         // np x dp, unit rows, zero padding
+  void* xlow = nullptr;          // np x dp bf16 / fp8 copy for the tensor-core path
+  float* xscale = nullptr;       // np fp8 row scales
+  double* norm = nullptr;        // n, ||x_i|| in FP64 accuracy
+  // K1 / K2
+  float* part_s = nullptr;       // n x P x K
+  int32_t* part_i = nullptr;
+  int32_t* knn_idx = nullptr;    // n x k1
+  float* knn_score = nullptr;
+  int32_t* fb_rows = nullptr;    // rows to redo exactly (count in status)
+  int32_t* fb_count = nullptr;
+  // K3
+  int32_t* indeg = nullptr;
+  int32_t* fill = nullptr;
+  int32_t* inptr = nullptr;      // n + 1
+  int32_t* insrc = nullptr;      // n * k1
+  int32_t* out_sorted = nullptr; // n * k1
+  int32_t* in_sorted = nullptr;  // n * k1
+  int32_t* rowcnt = nullptr;     // n
+  int32_t* h0ptr = nullptr;      // n + 1
+  int32_t* nbr = nullptr;        // n x (k2 + 1)
+  float* nbr_w = nullptr;        // n x (k2 + 1)
+  int32_t* nbr_n = nullptr;      // n
+  // padded-CSR feature buffers: slots 0 and 1 alternate between layers,
+  // slot 2 holds h^(0) (capacity 2 n k1)
+  int64_t* start[3] = {nullptr, nullptr, nullptr};  // n + 1 (exclusive scan; [n] = total)
+  int32_t* len[3] = {nullptr, nullptr, nullptr};
+  int32_t* col[3] = {nullptr, nullptr, nullptr};
+  float* val[3] = {nullptr, nullptr, nullptr};
+  int32_t* ub = nullptr;         // n
+  int32_t* big_rows = nullptr;   // n
+  int32_t* big_count = nullptr;
+  float* hash_keys_vals = nullptr; // global hash tables of the big-row path
+  float* rnorm = nullptr;        // n, 1/||h_i^(L)||
+  // K5 / K6
+  int32_t* colcnt = nullptr;     // n
+  int64_t* colptr = nullptr;     // n + 1
+  int32_t* csc_row = nullptr;
+  float* csc_val = nullptr;
+  uint32_t* rank_scratch = nullptr;
+  // scan scratch
+  int64_t* scan_tmp = nullptr;
+};
+
+struct Shape {
+  int64_t nq = 0, ng = 0, n = 0, np = 0;
+  int d = 0, dp = 0, dtype = 0;
+  int k1 = 0, k2 = 0, layers = 0, K = 0, P = 0;
+  int64_t topk = 0;
+  bool host_in = false, host_out = false;
+  bool knn_only = false;
+  int64_t cap_h = 0;       // elements per padded-CSR layer buffer
+  int64_t cap_csc = 0;
+  int hash_slots = 0;      // slots of each global hash table (big-row path)
+  int rank_ctas = 0;
+  int64_t rank_scratch_per_cta = 0;
+};
+
+struct StageTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<const char*> names;
+  cudaStream_t stream = nullptr;
+  void mark(const char* name);
+};
+
+}  // namespace rr
+
+struct rerank_ctx {
+  rerank_config cfg{};
+  int device = 0;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  char* ws = nullptr;          // device workspace block
+  size_t ws_bytes = 0;
+  long long* d_status = nullptr;  // device status block (rr::kStCount int64)
+  long long* h_status = nullptr;  // pinned host copy
+  rr::Tuning tune{};
+  std::string tune_path;
+  int64_t cap_h_hint = 0;      // layer-buffer capacity learned from earlier overflows
+  int64_t test_cap_h = 0;      // initial layer capacity forced by RERANK_TEST_CAP_H (tests only)
+  int64_t cap_csc_hint = 0;
+  rr::StageTimer timer;
+  std::vector<float> stage_ms;
+  std::vector<const char*> stage_names;
+  rerank_info info{};
+  int64_t launches = 0;
+  rr::Buffers buf{};
+  rr::Shape shape{};
+};
+
+namespace rr {
+
+// ---- stage launchers (each enqueues on `s`; no host synchronisation) ----
+int launch_normalize(const Shape& sh, const void* xq, const void* xg, float* xhat, double* norm,
+                      void* xlow, float* xscale, int precision, long long* status, cudaStream_t s);
+int launch_sim_fp32_topk(const Shape& sh, const float* xhat, float* part_s, int32_t* part_i,
+                          int sm_count, cudaStream_t s);
+int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat,
+                   const double* norm, const float* part_s, const int32_t* part_i, double eps_gemm,
+                   int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
+                   long long* status, cudaStream_t s);
+int launch_refine_fallback(const Shape& sh, const void* xq, const void* xg, const float* xhat,
+                            const double* norm, int32_t* knn_idx, float* knn_score,
+                            const int32_t* fb_rows, const int32_t* fb_count, float* scratch_s,
+                            int32_t* scratch_i, long long* status, int sm_count, cudaStream_t s);
+int launch_scan(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
+int launch_scan32(const int32_t* in, int64_t n, int32_t* out, cudaStream_t s);
+int launch_graph(const Shape& sh, const Buffers& b, float alpha, int aggregator, int feature,
+                  long long* status, cudaStream_t s);
+int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int aggregator,
+                      long long* status, int sm_count, const Tuning& t, cudaStream_t s);
+int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s);
+int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist,
+                 long long* status, int sm_count, const Tuning& t, cudaStream_t s);
+
+size_t rank_smem_bytes(int64_t ng, int threads);
+int propagate_warp_slots();
+
+}  // namespace rr

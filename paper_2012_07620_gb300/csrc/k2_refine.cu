@@ -1,0 +1,365 @@
+// K2: exact top-k1 neighbour lists (Eq. 8) from approximate candidates.
+//
+// The similarity stage returns, per row, K = k1 + m candidates ranked by an
+// approximate score g with a known error bound eps_g (FP32 GEMM: an FMA chain
+// of dp terms; BF16/FP8 GEMM: the quantisation bound).  For each row one warp
+//   1. merges the per-chunk candidate lists (P-way merge, ties to the lower
+//      index) and bounds every excluded column's approximate score by B;
+//   2. rescores each candidate in FP32 from the unit rows: each lane runs an
+//      FMA chain over dp/32 terms and the warp adds the 32 partials in a
+//      5-level tree, so |s - S| <= eps_r = (dp/32 + 10) u (u = 2^-24; the
+//      10 covers the tree and the rounding of the unit rows);
+//   3. sorts the candidates by (s desc, index asc);
+//   4. certifies the list: if s_(k1) - eps_r > B + eps_g, no excluded column
+//      can belong to the true top-k1 (otherwise the row is redone exactly by
+//      the fallback kernel below, which scores all n columns);
+//   5. finds runs of consecutive candidates whose s values are within 2 eps_r
+//      of each other and that reach into the top-k1; their members are
+//      recomputed in FP64 from the caller's raw features, cos = x_i.x_j /
+//      (||x_i|| ||x_j||), and each run is re-sorted by (FP64 value, index).
+//      Outside such runs the FP32 order is already the exact order.
+// Output: knn_idx[i][0..k1) and knn_score (the FP64 value where one was
+// computed, else s).  Self gets S_ii = 1 exactly.
+#include <cfloat>
+
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace rr {
+namespace {
+
+constexpr int KMAX = 64;
+constexpr int WPB = 8;
+
+struct WarpSmem {
+  int idx[KMAX];
+  float g[KMAX];
+  float s[KMAX];
+  double t[KMAX];
+  int ord[KMAX];
+  unsigned char need[KMAX];
+};
+
+struct RowIo {
+  const void* xq;
+  const void* xg;
+  int64_t nq;
+  int d;
+  int dtype;
+  const float* xhat;
+  int dp;
+  const double* norm;
+  int32_t* knn_idx;
+  float* knn_score;
+  long long* status;
+};
+
+__device__ __forceinline__ const void* raw_row(const RowIo& io, int64_t r, size_t& base) {
+  if (r < io.nq) {
+    base = size_t(r) * io.d;
+    return io.xq;
+  }
+  base = size_t(r - io.nq) * io.d;
+  return io.xg;
+}
+
+__device__ double dot_fp64_raw(const RowIo& io, int64_t a, int64_t b, int lane) {
+  size_t ba, bb;
+  const void* pa = raw_row(io, a, ba);
+  const void* pb = raw_row(io, b, bb);
+  double acc = 0.0;
+  for (int k = lane; k < io.d; k += kWarp)
+    acc = fma(double(load_feat(pa, io.dtype, ba + k)), double(load_feat(pb, io.dtype, bb + k)), acc);
+  return warp_sum(acc);
+}
+
+// Two FP32 dot products of unit rows at once (independent chains for memory parallelism).
+__device__ __forceinline__ void dot2_fp32(const float* xi, const float* y0, const float* y1, int dp, int lane,
+                                          float& r0, float& r1) {
+  const float4* a = reinterpret_cast<const float4*>(xi);
+  const float4* b0 = reinterpret_cast<const float4*>(y0);
+  const float4* b1 = reinterpret_cast<const float4*>(y1);
+  float acc0 = 0.f, acc1 = 0.f;
+  for (int q = lane; q < dp / 4; q += kWarp) {
+    const float4 x = __ldg(a + q), u = __ldg(b0 + q), v = __ldg(b1 + q);
+    acc0 = fmaf(x.x, u.x, acc0); acc0 = fmaf(x.y, u.y, acc0);
+    acc0 = fmaf(x.z, u.z, acc0); acc0 = fmaf(x.w, u.w, acc0);
+    acc1 = fmaf(x.x, v.x, acc1); acc1 = fmaf(x.y, v.y, acc1);
+    acc1 = fmaf(x.z, v.z, acc1); acc1 = fmaf(x.w, v.w, acc1);
+  }
+  r0 = warp_sum(acc0);
+  r1 = warp_sum(acc1);
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// P-way merge of sorted candidate lists src[p*K .. p*K+K) for p < P (P <= 32),
+// one list per lane.  Fills w.idx/w.g with the best K; returns the count and
+// the bound B on every candidate that was not taken.
+__device__ int merge_lists(WarpSmem& w, const float* ls, const int32_t* li, int P, int K, int lane, float& B) {
+  int head = 0;
+  float hs = -FLT_MAX;
+  int hi = kInvalidIdx;
+  if (lane < P) {
+    hs = ls[lane * K];
+    hi = li[lane * K];
+  }
+  int cnt = 0;
+  for (; cnt < K; ++cnt) {
+    float bs = hs;
+    int bi = hi, bl = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float os = __shfl_xor_sync(kFull, bs, o);
+      const int oi = __shfl_xor_sync(kFull, bi, o);
+      const int ol = __shfl_xor_sync(kFull, bl, o);
+      if (ranks_before(os, oi, bs, bi)) {
+        bs = os;
+        bi = oi;
+        bl = ol;
+      }
+    }
+    if (bi == kInvalidIdx) break;
+    if (lane == 0) {
+      w.idx[cnt] = bi;
+      w.g[cnt] = bs;
+    }
+    if (lane == bl) {
+      ++head;
+      if (head < K) {
+        hs = ls[lane * K + head];
+        hi = li[lane * K + head];
+      } else {
+        hs = -FLT_MAX;
+        hi = kInvalidIdx;
+      }
+    }
+  }
+  float b = hi != kInvalidIdx ? hs : -FLT_MAX;
+  if (lane < P && li[lane * K + K - 1] != kInvalidIdx) b = fmaxf(b, ls[lane * K + K - 1]);
+  B = warp_max(b);
+  __syncwarp();
+  return cnt;
+}
+
+// Steps 2-5 for row i on candidates w.idx[0..K).  Returns false when the
+// candidate list cannot be certified (then nothing is written unless `last`).
+__device__ bool refine_warp(WarpSmem& w, int K, int64_t i, int k1, float B, double eps_g, double eps_r,
+                            const RowIo& io, bool last, int lane) {
+  const float* xi = io.xhat + size_t(i) * io.dp;
+  for (int c = 0; c < K; c += 2) {
+    const int j0 = w.idx[c];
+    const int j1 = c + 1 < K ? w.idx[c + 1] : j0;
+    float v0, v1;
+    dot2_fp32(xi, io.xhat + size_t(j0) * io.dp, io.xhat + size_t(j1) * io.dp, io.dp, lane, v0, v1);
+    if (lane == 0) {
+      w.s[c] = j0 == i ? 1.0f : v0;
+      if (c + 1 < K) w.s[c + 1] = j1 == i ? 1.0f : v1;
+    }
+  }
+  for (int c = lane; c < K; c += kWarp) w.need[c] = 0;
+  __syncwarp();
+  for (int c = lane; c < K; c += kWarp) {
+    const float sc = w.s[c];
+    const int ic = w.idx[c];
+    int r = 0;
+    for (int e = 0; e < K; ++e) r += ranks_before(w.s[e], w.idx[e], sc, ic) ? 1 : 0;
+    w.ord[r] = c;
+  }
+  __syncwarp();
+
+  bool ok = true;
+  if (B > -FLT_MAX) ok = double(w.s[w.ord[k1 - 1]]) - eps_r > double(B) + eps_g;
+  if (!ok && !last) return false;
+
+  // Runs of near-equal FP32 scores that reach into the top-k1.
+  if (lane == 0) {
+    int r = 0;
+    while (r < K) {
+      int r1 = r;
+      while (r1 + 1 < K && double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r) ++r1;
+      if (r1 > r && r < k1)
+        for (int q = r; q <= r1; ++q) w.need[w.ord[q]] = 1;
+      r = r1 + 1;
+    }
+  }
+  __syncwarp();
+  int nneed = 0;
+  for (int c = 0; c < K; ++c) {
+    if (!w.need[c]) continue;
+    const int j = w.idx[c];
+    double t = 1.0;
+    if (j != i) t = dot_fp64_raw(io, i, j, lane) / (io.norm[i] * io.norm[j]);
+    if (lane == 0) w.t[c] = t;
+    ++nneed;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    if (nneed) atomicAdd(reinterpret_cast<unsigned long long*>(io.status + kStFp64), (unsigned long long)nneed);
+    // Re-sort each run by (FP64 value desc, index asc); runs are maximal
+    // blocks of consecutive needed positions whose gaps are <= 2 eps_r.
+    int r = 0;
+    while (r < K) {
+      if (!w.need[w.ord[r]]) {
+        ++r;
+        continue;
+      }
+      int r1 = r;
+      while (r1 + 1 < K && w.need[w.ord[r1 + 1]] &&
+             double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r)
+        ++r1;
+      for (int a = r + 1; a <= r1; ++a) {
+        const int c = w.ord[a];
+        int b = a;
+        while (b > r && ranks_before(w.t[c], w.idx[c], w.t[w.ord[b - 1]], w.idx[w.ord[b - 1]])) {
+          w.ord[b] = w.ord[b - 1];
+          --b;
+        }
+        w.ord[b] = c;
+      }
+      r = r1 + 1;
+    }
+  }
+  __syncwarp();
+  for (int r = lane; r < k1; r += kWarp) {
+    const int c = w.ord[r];
+    io.knn_idx[size_t(i) * k1 + r] = w.idx[c];
+    io.knn_score[size_t(i) * k1 + r] = w.need[c] ? float(w.t[c]) : w.s[c];
+  }
+  if (!ok && lane == 0) set_error(io.status, kErrCertify);
+  return ok;
+}
+
+__global__ void __launch_bounds__(WPB * kWarp)
+k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* __restrict__ part_i, int P,
+          int K, int k1, double eps_g, double eps_r, int32_t* fb_rows, int32_t* fb_count) {
+  __shared__ WarpSmem sm[WPB];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = int64_t(blockIdx.x) * WPB + wib;
+  if (i >= n) return;
+  WarpSmem& w = sm[wib];
+  float B;
+  const size_t base = size_t(i) * P * K;
+  const int cnt = merge_lists(w, part_s + base, part_i + base, P, K, lane, B);
+  if (cnt == n) B = -FLT_MAX;  // every column is a candidate
+  if (cnt < k1) {
+    if (lane == 0) set_error(io.status, kErrInternal);
+    return;
+  }
+  const bool ok = refine_warp(w, cnt, i, k1, B, eps_g, eps_r, io, false, lane);
+  if (!ok && lane == 0) {
+    const int slot = atomicAdd(fb_count, 1);
+    fb_rows[slot] = int32_t(i);
+    atomicAdd(reinterpret_cast<unsigned long long*>(io.status + kStFallback), 1ull);
+  }
+}
+
+// Exact fallback: score all n columns of a flagged row with the accurate FP32
+// dot, keep per-warp top-K lists, merge them, then refine with eps_g = eps_r.
+constexpr int FB_WARPS = 32;
+__global__ void __launch_bounds__(FB_WARPS * kWarp)
+k2_fallback(RowIo io, int64_t n, int K, int k1, double eps_r, const int32_t* fb_rows, const int32_t* fb_count,
+            float* scratch_s, int32_t* scratch_i) {
+  __shared__ WarpSmem w;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int count = *fb_count;
+  for (int f = blockIdx.x; f < count; f += gridDim.x) {
+    const int64_t i = fb_rows[f];
+    float* ls = scratch_s + (size_t(blockIdx.x) * FB_WARPS + warp) * K;
+    int32_t* li = scratch_i + (size_t(blockIdx.x) * FB_WARPS + warp) * K;
+    for (int e = lane; e < K; e += kWarp) {
+      ls[e] = -FLT_MAX;
+      li[e] = kInvalidIdx;
+    }
+    __syncwarp();
+    float thr_s = -FLT_MAX;
+    int thr_i = kInvalidIdx;
+    const float* xi = io.xhat + size_t(i) * io.dp;
+    for (int64_t c0 = warp; c0 < n; c0 += 2 * FB_WARPS) {
+      const int64_t c1 = c0 + FB_WARPS < n ? c0 + FB_WARPS : c0;
+      float v[2];
+      dot2_fp32(xi, io.xhat + size_t(c0) * io.dp, io.xhat + size_t(c1) * io.dp, io.dp, lane, v[0], v[1]);
+      const int64_t cs[2] = {c0, c1};
+      const int m = c1 != c0 ? 2 : 1;
+      if (lane == 0) {
+        for (int q = 0; q < m; ++q) {
+          const int col = int(cs[q]);
+          const float s = col == i ? 1.0f : v[q];
+          if (!ranks_before(s, col, thr_s, thr_i)) continue;
+          int p = K - 1;
+          while (p > 0 && ranks_before(s, col, ls[p - 1], li[p - 1])) {
+            ls[p] = ls[p - 1];
+            li[p] = li[p - 1];
+            --p;
+          }
+          ls[p] = s;
+          li[p] = col;
+          thr_s = ls[K - 1];
+          thr_i = li[K - 1];
+        }
+      }
+      __syncwarp();
+    }
+    __threadfence_block();
+    __syncthreads();
+    if (warp == 0) {
+      float B;
+      const int cnt = merge_lists(w, scratch_s + size_t(blockIdx.x) * FB_WARPS * K,
+                                  scratch_i + size_t(blockIdx.x) * FB_WARPS * K, FB_WARPS, K, lane, B);
+      if (cnt == n) B = -FLT_MAX;
+      if (cnt >= k1) refine_warp(w, cnt, i, k1, B, eps_r, eps_r, io, true, lane);
+      else if (lane == 0) set_error(io.status, kErrInternal);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+static RowIo make_io(const Shape& sh, const void* xq, const void* xg, const float* xhat, const double* norm,
+                     int32_t* knn_idx, float* knn_score, long long* status) {
+  RowIo io;
+  io.xq = xq;
+  io.xg = xg;
+  io.nq = sh.nq;
+  io.d = sh.d;
+  io.dtype = sh.dtype;
+  io.xhat = xhat;
+  io.dp = sh.dp;
+  io.norm = norm;
+  io.knn_idx = knn_idx;
+  io.knn_score = knn_score;
+  io.status = status;
+  return io;
+}
+
+double rescore_eps(int dp) { return (dp / 32 + 10) * kU32 * 1.01; }
+
+int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat, const double* norm,
+                   const float* part_s, const int32_t* part_i, double eps_gemm, int32_t* knn_idx,
+                   float* knn_score, int32_t* fb_rows, int32_t* fb_count, long long* status, cudaStream_t s) {
+  RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
+  const unsigned blocks = unsigned((sh.n + WPB - 1) / WPB);
+  k2_refine<<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, sh.P, sh.K, sh.k1, eps_gemm,
+                                           rescore_eps(sh.dp), fb_rows, fb_count);
+  return 1;
+}
+
+int launch_refine_fallback(const Shape& sh, const void* xq, const void* xg, const float* xhat,
+                            const double* norm, int32_t* knn_idx, float* knn_score, const int32_t* fb_rows,
+                            const int32_t* fb_count, float* scratch_s, int32_t* scratch_i, long long* status,
+                            int sm_count, cudaStream_t s) {
+  RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
+  k2_fallback<<<sm_count, FB_WARPS * kWarp, 0, s>>>(io, sh.n, sh.K, sh.k1, rescore_eps(sh.dp), fb_rows, fb_count,
+                                                    scratch_s, scratch_i);
+  return 1;
+}
+
+int refine_kmax() { return KMAX; }
+int fallback_warps() { return FB_WARPS; }
+
+}  // namespace rr

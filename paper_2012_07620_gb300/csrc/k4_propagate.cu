@@ -1,0 +1,305 @@
+// K4: one message-passing layer (Eq. 13-14, sum or mean aggregator) followed
+// by L2 normalisation (Sec. 3.3), on sparse vertex features.
+//
+//   h_i <- normalise( sum_{(j, c_j) in M(i)} c_j h_j )
+//
+// where M(i) is the message list built by K3 (N(i, k2) with c_j = e_ij^alpha,
+// the residual h_i folded into c_i).  Features are stored as padded CSR: row
+// i occupies [start_i, start_i + len_i) of (col, val) with columns ascending.
+// start_i is an exclusive scan of ub_i = sum_j len_j, an upper bound on the
+// output row, so every row can be written without a second pass.
+//
+// Rows with ub_i <= 1024 (almost all): one warp per row with a private
+// open-addressing hash table in shared memory (columns as keys).  The warp
+// walks the message list in order and adds c_j * val into the table, one
+// list at a time, so every output value is summed in message-list order and
+// the result does not depend on scheduling.  The occupied slots are
+// compacted, sorted by column (bitonic), scaled by 1/||row|| and written.
+// Larger rows: one CTA per row with a dense accumulator and a bitmap of
+// touched columns in global memory; the bitmap scan emits columns in order.
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace rr {
+namespace {
+
+constexpr int WSLOTS = 2048;  // hash slots per warp
+constexpr int KEY_EMPTY = -1;
+constexpr int BIG_THREADS = 256;
+
+__global__ void k4_ub(const int32_t* __restrict__ nbr, const int32_t* __restrict__ nbr_n, int k2p1,
+                      const int32_t* __restrict__ len, int64_t n, int32_t* __restrict__ ub,
+                      int32_t* __restrict__ big_rows, int32_t* __restrict__ big_count,
+                      const long long* __restrict__ status) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (status[kStErr] & kErrOverflow) {
+    ub[i] = 0;
+    return;
+  }
+  int64_t u = 0;
+  const int m = nbr_n[i];
+  for (int q = 0; q < m; ++q) u += len[nbr[i * k2p1 + q]];
+  if (u > n) u = n;
+  ub[i] = int32_t(u);
+  if (u > WSLOTS / 2) big_rows[atomicAdd(big_count, 1)] = int32_t(i);
+}
+
+__device__ __forceinline__ bool capacity_ok(const int64_t* dstart, int64_t n, int64_t cap, long long* status) {
+  if (status[kStErr] & kErrOverflow) return false;
+  const int64_t need = dstart[n];
+  if (need > cap) {
+    if (threadIdx.x == 0) {
+      set_error(status, kErrOverflow);
+      atomicMax(reinterpret_cast<unsigned long long*>(status + kStNeed), (unsigned long long)need);
+    }
+    return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void hash_add(volatile int* keys, float* vals, int mask, int shift, int col, float v,
+                                         long long* status) {
+  const unsigned h = (unsigned(col) * 2654435761u) >> shift;
+  for (int probe = 0; probe <= mask; ++probe) {
+    const int slot = int((h + unsigned(probe)) & unsigned(mask));
+    const int k = keys[slot];
+    if (k == col) {
+      vals[slot] += v;
+      return;
+    }
+    if (k == KEY_EMPTY) {
+      const int old = atomicCAS(const_cast<int*>(keys) + slot, KEY_EMPTY, col);
+      if (old == KEY_EMPTY || old == col) {
+        vals[slot] += v;
+        return;
+      }
+    }
+  }
+  set_error(status, kErrInternal);
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+__global__ void __launch_bounds__(256)
+k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen, const int32_t* __restrict__ scol,
+             const float* __restrict__ sval, const int32_t* __restrict__ nbr, const float* __restrict__ nbr_w,
+             const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ ub,
+             const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen, int32_t* __restrict__ dcol,
+             float* __restrict__ dval, int64_t n, int64_t cap, long long* __restrict__ status) {
+  extern __shared__ int smem_i[];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  volatile int* keys = smem_i + wib * WSLOTS * 2;
+  float* vals = reinterpret_cast<float*>(smem_i + wib * WSLOTS * 2 + WSLOTS);
+  if (!capacity_ok(dstart, n, cap, status)) return;
+  for (int s = lane; s < WSLOTS; s += kWarp) {
+    keys[s] = KEY_EMPTY;
+    vals[s] = 0.f;
+  }
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t i = int64_t(blockIdx.x) * nw + wib; i < n; i += int64_t(gridDim.x) * nw) {
+    const int u = ub[i];
+    if (u > WSLOTS / 2) continue;
+    const int T = next_pow2(max(64, 2 * u));
+    const int mask = T - 1, shift = 32 - (31 - __clz(T));
+    const int m = nbr_n[i];
+    for (int q = 0; q < m; ++q) {
+      const int32_t j = nbr[i * k2p1 + q];
+      const float cj = nbr_w[i * k2p1 + q];
+      const int64_t a = sstart[j];
+      const int lj = slen[j];
+      for (int e0 = 0; e0 < lj; e0 += kWarp) {
+        const int e = e0 + lane;
+        if (e < lj) hash_add(keys, vals, mask, shift, scol[a + e], cj * sval[a + e], status);
+        __syncwarp();
+      }
+    }
+    // Compact occupied slots to the front (order-preserving, in place).
+    int cnt = 0;
+    for (int s0 = 0; s0 < T; s0 += kWarp) {
+      const int k = keys[s0 + lane];
+      const float v = vals[s0 + lane];
+      const bool occ = k != KEY_EMPTY;
+      const unsigned bal = __ballot_sync(kFull, occ);
+      const int pos = cnt + __popc(bal & lt);
+      __syncwarp();
+      if (occ) {
+        keys[pos] = k;
+        vals[pos] = v;
+      }
+      cnt += __popc(bal);
+      __syncwarp();
+    }
+    const int P2 = next_pow2(max(cnt, 2));
+    for (int s = cnt + lane; s < P2; s += kWarp) keys[s] = kInvalidIdx;
+    __syncwarp();
+    // Bitonic sort of (key, val) by key over P2 slots.
+    for (int k = 2; k <= P2; k <<= 1) {
+      for (int jj = k >> 1; jj > 0; jj >>= 1) {
+        for (int t = lane; t < P2 / 2; t += kWarp) {
+          const int i1 = (t / jj) * 2 * jj + (t % jj), i2 = i1 + jj;
+          const bool up = (i1 & k) == 0;
+          const int ka = keys[i1], kb = keys[i2];
+          if ((ka > kb) == up) {
+            keys[i1] = kb;
+            keys[i2] = ka;
+            const float va = vals[i1];
+            vals[i1] = vals[i2];
+            vals[i2] = va;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    float ss = 0.f;
+    for (int p = lane; p < cnt; p += kWarp) ss = fmaf(vals[p], vals[p], ss);
+    ss = warp_sum(ss);
+    const float inv = 1.0f / sqrtf(ss);
+    const int64_t o = dstart[i];
+    for (int p = lane; p < cnt; p += kWarp) {
+      dcol[o + p] = keys[p];
+      dval[o + p] = vals[p] * inv;
+    }
+    if (lane == 0) dlen[i] = cnt;
+    __syncwarp();
+    for (int s = lane; s < T; s += kWarp) {
+      keys[s] = KEY_EMPTY;
+      vals[s] = 0.f;
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(BIG_THREADS)
+k4_spmm_big(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen, const int32_t* __restrict__ scol,
+            const float* __restrict__ sval, const int32_t* __restrict__ nbr, const float* __restrict__ nbr_w,
+            const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ big_rows,
+            const int32_t* __restrict__ big_count, const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen,
+            int32_t* __restrict__ dcol, float* __restrict__ dval, int64_t n, int64_t cap, float* __restrict__ dense,
+            uint32_t* __restrict__ bits, long long* __restrict__ status) {
+  __shared__ int scan_s[BIG_THREADS];
+  __shared__ float red_s[BIG_THREADS];
+  if (!capacity_ok(dstart, n, cap, status)) return;
+  const int tid = threadIdx.x;
+  const int64_t nwords = (n + 31) / 32;
+  float* acc = dense + size_t(blockIdx.x) * n;
+  uint32_t* bm = bits + size_t(blockIdx.x) * nwords;
+  const int count = *big_count;
+  const int64_t wpt = (nwords + BIG_THREADS - 1) / BIG_THREADS;
+  const int64_t w0 = tmin<int64_t>(nwords, tid * wpt), w1 = tmin<int64_t>(nwords, w0 + wpt);
+  for (int f = blockIdx.x; f < count; f += gridDim.x) {
+    const int64_t i = big_rows[f];
+    const int m = nbr_n[i];
+    for (int q = 0; q < m; ++q) {
+      const int32_t j = nbr[i * k2p1 + q];
+      const float cj = nbr_w[i * k2p1 + q];
+      const int64_t a = sstart[j];
+      const int lj = slen[j];
+      for (int e = tid; e < lj; e += BIG_THREADS) {
+        const int c = scol[a + e];
+        acc[c] += cj * sval[a + e];
+        atomicOr(&bm[c >> 5], 1u << (c & 31));
+      }
+      __syncthreads();
+    }
+    int mine = 0;
+    for (int64_t w = w0; w < w1; ++w) mine += __popc(bm[w]);
+    scan_s[tid] = mine;
+    __syncthreads();
+    for (int o = 1; o < BIG_THREADS; o <<= 1) {
+      const int v = tid >= o ? scan_s[tid - o] : 0;
+      __syncthreads();
+      scan_s[tid] += v;
+      __syncthreads();
+    }
+    const int total = scan_s[BIG_THREADS - 1];
+    int pos = scan_s[tid] - mine;
+    const int64_t o = dstart[i];
+    float ss = 0.f;
+    for (int64_t w = w0; w < w1; ++w) {
+      uint32_t b = bm[w];
+      while (b) {
+        const int bit = __ffs(b) - 1;
+        b &= b - 1;
+        const int c = int(w * 32 + bit);
+        const float v = acc[c];
+        ss = fmaf(v, v, ss);
+        dcol[o + pos] = c;
+        dval[o + pos] = v;
+        acc[c] = 0.f;
+        ++pos;
+      }
+      bm[w] = 0u;
+    }
+    red_s[tid] = ss;
+    __syncthreads();
+    for (int s = BIG_THREADS / 2; s > 0; s >>= 1) {
+      if (tid < s) red_s[tid] += red_s[tid + s];
+      __syncthreads();
+    }
+    const float inv = 1.0f / sqrtf(red_s[0]);
+    for (int p = tid; p < total; p += BIG_THREADS) dval[o + p] *= inv;
+    if (tid == 0) dlen[i] = total;
+    __syncthreads();
+  }
+}
+
+__global__ void k4_row_norms(const int64_t* __restrict__ start, const int32_t* __restrict__ len,
+                             const float* __restrict__ val, int64_t n, float* __restrict__ rn,
+                             const long long* __restrict__ status) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  // After an overflowing layer the row lengths of its output were never written.
+  if (i >= n || (status[kStErr] & kErrOverflow)) return;
+  const int64_t a = start[i];
+  const int m = len[i];
+  float ss = 0.f;
+  for (int p = lane; p < m; p += kWarp) ss = fmaf(val[a + p], val[a + p], ss);
+  ss = warp_sum(ss);
+  if (lane == 0) rn[i] = 1.0f / sqrtf(ss);
+}
+
+}  // namespace
+
+int propagate_warp_slots() { return WSLOTS; }
+
+int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int aggregator, long long* status,
+                      int sm_count, const Tuning& t, cudaStream_t s) {
+  (void)aggregator;
+  const int64_t n = sh.n;
+  const int k2p1 = sh.k2 + 1;
+  const int T = 256;
+  cudaMemsetAsync(b.big_count, 0, sizeof(int32_t), s);
+  k4_ub<<<unsigned((n + T - 1) / T), T, 0, s>>>(b.nbr, b.nbr_n, k2p1, b.len[src], n, b.ub, b.big_rows, b.big_count,
+                                                 status);
+  launch_scan(b.ub, n, b.start[dst], s);
+  const int warps = t.prop_warps;
+  const size_t smem = size_t(warps) * WSLOTS * 2 * sizeof(int);
+  cudaFuncSetAttribute(k4_spmm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const int64_t blocks_needed = (n + warps - 1) / warps;
+  const int per_sm = smem ? int((227 * 1024) / smem) : 1;
+  const unsigned blocks = unsigned(tmin<int64_t>(blocks_needed, int64_t(sm_count) * (per_sm > 0 ? per_sm : 1)));
+  k4_spmm_warp<<<blocks, warps * kWarp, smem, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
+                                                   b.nbr_n, k2p1, b.ub, b.start[dst], b.len[dst], b.col[dst],
+                                                   b.val[dst], n, sh.cap_h, status);
+  k4_spmm_big<<<sm_count, BIG_THREADS, 0, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
+                                               b.nbr_n, k2p1, b.big_rows, b.big_count, b.start[dst], b.len[dst],
+                                               b.col[dst], b.val[dst], n, sh.cap_h, b.hash_keys_vals,
+                                               reinterpret_cast<uint32_t*>(b.hash_keys_vals + size_t(sm_count) * n),
+                                               status);
+  return 4;
+}
+
+int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s) {
+  const int T = 256;
+  k4_row_norms<<<unsigned((sh.n * kWarp + T - 1) / T), T, 0, s>>>(b.start[src], b.len[src], b.val[src], sh.n,
+                                                                   b.rnorm, status);
+  return 1;
+}
+
+}  // namespace rr

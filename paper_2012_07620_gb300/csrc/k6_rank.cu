@@ -1,0 +1,315 @@
+// K5 + K6: the final ranking (Alg. 1 step 7): for every query q the gallery
+// sorted by cos(h_q, h_g), descending, ties to the lower gallery index;
+// returned as (gallery index, 1 - cos).
+//
+// K5 transposes the gallery rows of H (scaled to unit norm) into CSC, so the
+// column c lists every gallery vertex g with h_g[c] != 0.
+// K6 takes one query per CTA and computes all of its scores at once,
+// Gustavson style: s_g = sum_{c in supp(h_q)} h_q[c] * h_g[c].  Products are
+// accumulated as unsigned fixed point (2^-31 units) with shared-memory atomics;
+// integer addition is associative, so the score does not depend on the order
+// in which warps add their terms.  Zero scores (disjoint supports, the bulk of
+// the gallery) are exact.  The non-zero scores are compacted in gallery
+// order and put in order by a stable LSD radix sort on the bit-inverted score
+// (four 8-bit passes, per-warp digit histograms, __match_any_sync ranks), which
+// keeps equal scores in ascending gallery index; the zero tail follows in
+// ascending gallery index.
+#include "common.cuh"
+#include "internal.hpp"
+
+namespace rr {
+namespace {
+
+constexpr int RT = 1024;                // threads per ranking CTA
+constexpr int RW = RT / kWarp;
+constexpr int SORT_CAP = 4096;          // non-zeros sorted in shared memory
+constexpr float kFix = 2147483648.0f;   // 2^31
+constexpr float kUnfix = 4.656612873077393e-10f;  // 2^-31
+
+__global__ void k5_count(const int64_t* __restrict__ start, const int32_t* __restrict__ len,
+                         const int32_t* __restrict__ col, int64_t nq, int64_t n, int32_t* __restrict__ colcnt,
+                         const long long* __restrict__ status) {
+  const int64_t r = nq + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= n || (status[kStErr] & kErrOverflow)) return;
+  const int64_t a = start[r];
+  const int m = len[r];
+  for (int p = lane; p < m; p += kWarp) atomicAdd(&colcnt[col[a + p]], 1);
+}
+
+__global__ void k5_fill(const int64_t* __restrict__ start, const int32_t* __restrict__ len,
+                        const int32_t* __restrict__ col, const float* __restrict__ val, const float* __restrict__ rn,
+                        int64_t nq, int64_t n, const int64_t* __restrict__ colptr, int32_t* __restrict__ fill,
+                        int32_t* __restrict__ csc_row, float* __restrict__ csc_val,
+                        const long long* __restrict__ status) {
+  const int64_t r = nq + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (r >= n || (status[kStErr] & kErrOverflow)) return;
+  const int64_t a = start[r];
+  const int m = len[r];
+  const float s = rn[r];
+  for (int p = lane; p < m; p += kWarp) {
+    const int c = col[a + p];
+    const int64_t pos = colptr[c] + atomicAdd(&fill[c], 1);
+    csc_row[pos] = int32_t(r - nq);
+    csc_val[pos] = val[a + p] * s;
+  }
+}
+
+// Exclusive block scan of one int per thread; returns the total.
+__device__ int block_exscan(int v, int* tmp, int& excl) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = lane < RW ? tmp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, s, o);
+      if (lane >= o) s += y;
+    }
+    tmp[lane] = s;
+  }
+  __syncthreads();
+  excl = x - v + (w ? tmp[w - 1] : 0);
+  const int total = tmp[RW - 1];
+  __syncthreads();
+  return total;
+}
+
+// Stable LSD radix sort of (key, val) ascending by key; returns the buffer pair holding the result.
+__device__ void block_radix_sort(uint32_t*& keys, uint32_t*& vals, uint32_t*& tkeys, uint32_t*& tvals, int cnt,
+                                 uint32_t* hist, int* tmp) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int seg = (cnt + RW - 1) / RW;
+  const int a = min(cnt, w * seg), b = min(cnt, a + seg);
+  for (int shift = 0; shift < 32; shift += 8) {
+    for (int e = t; e < RW * 256; e += RT) hist[e] = 0;
+    __syncthreads();
+    for (int p = a + lane; p < b; p += kWarp) atomicAdd(&hist[w * 256 + ((keys[p] >> shift) & 255)], 1u);
+    __syncthreads();
+    int tot = 0;
+    if (t < 256) {
+      for (int ww = 0; ww < RW; ++ww) {
+        const uint32_t c = hist[ww * 256 + t];
+        hist[ww * 256 + t] = uint32_t(tot);
+        tot += int(c);
+      }
+    }
+    int base;
+    const int all = block_exscan(t < 256 ? tot : 0, tmp, base);
+    (void)all;
+    // A digit that holds every key: this pass would not move anything.
+    __shared__ int skip;
+    if (t == 0) skip = 0;
+    __syncthreads();
+    if (t < 256 && tot == cnt) skip = 1;
+    __syncthreads();
+    if (skip) continue;
+    if (t < 256)
+      for (int ww = 0; ww < RW; ++ww) hist[ww * 256 + t] += uint32_t(base);
+    __syncthreads();
+    for (int p0 = a; p0 < b; p0 += kWarp) {
+      const int p = p0 + lane;
+      const bool valid = p < b;
+      const uint32_t k = valid ? keys[p] : 0u;
+      const uint32_t v = valid ? vals[p] : 0u;
+      const int d = valid ? int((k >> shift) & 255) : 256 + lane;
+      const unsigned peers = __match_any_sync(kFull, d);
+      const int rank = __popc(peers & lt);
+      const uint32_t pos = valid ? hist[w * 256 + d] + uint32_t(rank) : 0u;
+      __syncwarp();
+      if (valid) {
+        tkeys[pos] = k;
+        tvals[pos] = v;
+        if ((peers & lt) == 0) hist[w * 256 + d] += uint32_t(__popc(peers));
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    uint32_t* x = keys; keys = tkeys; tkeys = x;
+    x = vals; vals = tvals; tvals = x;
+  }
+}
+
+struct RankArgs {
+  const int64_t* start;
+  const int32_t* len;
+  const int32_t* col;
+  const float* val;
+  const float* rn;
+  const int64_t* colptr;
+  const int32_t* csc_row;
+  const float* csc_val;
+  int64_t nq, ng, topk;
+  int32_t* out_idx;
+  float* out_dist;
+  uint32_t* gscratch;   // per CTA: acc (ng) [if !acc_smem] + 4 * ng sort buffers
+  int acc_smem;
+  long long* status;
+};
+
+__global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
+  extern __shared__ uint32_t sm[];
+  if (A.status[kStErr] & kErrOverflow) return;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int64_t ng = A.ng;
+  const int nwords = int((ng + 31) / 32);
+  uint32_t* hist = sm;                                   // RW * 256
+  int* tmp = reinterpret_cast<int*>(hist + RW * 256);    // 32
+  uint32_t* bits = reinterpret_cast<uint32_t*>(tmp + 32);  // nwords
+  uint32_t* skeys = bits + ((nwords + 3) & ~3);          // SORT_CAP
+  uint32_t* svals = skeys + SORT_CAP;                    // SORT_CAP
+  uint32_t* sacc = svals + SORT_CAP;                     // ng (when acc_smem)
+  uint32_t* gbase = A.gscratch + size_t(blockIdx.x) * (5 * size_t(ng));
+  uint32_t* acc = A.acc_smem ? sacc : gbase;
+  uint32_t* gk0 = gbase + ng;
+  uint32_t* gv0 = gk0 + ng;
+  uint32_t* gk1 = gv0 + ng;
+  uint32_t* gv1 = gk1 + ng;
+  const int64_t T = A.topk;
+
+  for (int64_t q = blockIdx.x; q < A.nq; q += gridDim.x) {
+    for (int64_t g = t; g < ng; g += RT) acc[g] = 0u;
+    __syncthreads();
+    const int64_t a = A.start[q];
+    const int m = A.len[q];
+    const float rq = A.rn[q];
+    for (int e = w; e < m; e += RW) {
+      const int c = A.col[a + e];
+      const float v = A.val[a + e] * rq;
+      const int64_t p0 = A.colptr[c], p1 = A.colptr[c + 1];
+      for (int64_t p = p0 + lane; p < p1; p += kWarp) {
+        const float prod = v * A.csc_val[p];
+        atomicAdd(&acc[A.csc_row[p]], __float2uint_rn(prod * kFix));
+      }
+    }
+    __syncthreads();
+    // Non-zero bitmap, one word per thread step.
+    for (int wd = t; wd < nwords; wd += RT) {
+      uint32_t b = 0u;
+      const int64_t g0 = int64_t(wd) * 32;
+      for (int k = 0; k < 32; ++k) {
+        const int64_t g = g0 + k;
+        if (g < ng && acc[g] != 0u) b |= 1u << k;
+      }
+      bits[wd] = b;
+    }
+    __syncthreads();
+    // Compact non-zeros in gallery order: key = ~acc (ascending = score desc), val = g.
+    const int64_t gc = (ng + RT - 1) / RT;
+    const int64_t ga = tmin<int64_t>(ng, t * gc), gb = tmin<int64_t>(ng, ga + gc);
+    int mine = 0;
+    for (int64_t g = ga; g < gb; ++g) mine += acc[g] != 0u;
+    int off;
+    const int cnt = block_exscan(mine, tmp, off);
+    const bool small = cnt <= SORT_CAP && A.acc_smem && ng >= 2 * int64_t(cnt);
+    uint32_t* k0 = small ? skeys : gk0;
+    uint32_t* v0 = small ? svals : gv0;
+    for (int64_t g = ga; g < gb; ++g) {
+      const uint32_t x = acc[g];
+      if (x != 0u) {
+        k0[off] = ~x;
+        v0[off] = uint32_t(g);
+        ++off;
+      }
+    }
+    __syncthreads();
+    uint32_t* k1 = small ? acc : gk1;
+    uint32_t* v1 = small ? acc + cnt : gv1;
+    block_radix_sort(k0, v0, k1, v1, cnt, hist, tmp);
+    // Sorted non-zeros, then the zero tail in gallery order.
+    const int64_t nout = tmin<int64_t>(T, cnt);
+    for (int64_t p = t; p < nout; p += RT) {
+      const float s = __uint2float_rn(~k0[p]) * kUnfix;
+      A.out_idx[q * T + p] = int32_t(v0[p]);
+      A.out_dist[q * T + p] = 1.0f - s;
+    }
+    if (T > cnt) {
+      const int wc = (nwords + RT - 1) / RT;
+      const int wa = min(nwords, t * wc), wb = min(nwords, wa + wc);
+      int z = 0;
+      for (int wd = wa; wd < wb; ++wd) {
+        const int valid = int(tmin<int64_t>(32, ng - int64_t(wd) * 32));
+        const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
+        z += __popc(~bits[wd] & vm);
+      }
+      int zoff;
+      block_exscan(z, tmp, zoff);
+      int64_t pos = cnt + zoff;
+      for (int wd = wa; wd < wb && pos < T; ++wd) {
+        const int valid = int(tmin<int64_t>(32, ng - int64_t(wd) * 32));
+        const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
+        uint32_t zb = ~bits[wd] & vm;
+        while (zb && pos < T) {
+          const int bit = __ffs(zb) - 1;
+          zb &= zb - 1;
+          A.out_idx[q * T + pos] = int32_t(int64_t(wd) * 32 + bit);
+          A.out_dist[q * T + pos] = 1.0f;
+          ++pos;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t rank_smem_fixed(int64_t ng) {
+  const int64_t nwords = (ng + 31) / 32;
+  return sizeof(uint32_t) * (RW * 256 + 32 + ((nwords + 3) & ~int64_t(3)) + 2 * SORT_CAP);
+}
+
+}  // namespace
+
+size_t rank_smem_bytes(int64_t ng, int threads) {
+  (void)threads;
+  const size_t fixed = rank_smem_fixed(ng);
+  const size_t with_acc = fixed + sizeof(uint32_t) * size_t(ng);
+  return with_acc <= 227 * 1024 ? with_acc : fixed;
+}
+
+int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist, long long* status,
+                 int sm_count, const Tuning& tune, cudaStream_t s) {
+  (void)tune;
+  const int64_t n = sh.n, nq = sh.nq, ng = sh.ng;
+  const int T = 256;
+  cudaMemsetAsync(b.colcnt, 0, sizeof(int32_t) * (n + 1), s);
+  k5_count<<<unsigned((ng * kWarp + T - 1) / T), T, 0, s>>>(b.start[src], b.len[src], b.col[src], nq, n, b.colcnt,
+                                                            status);
+  launch_scan(b.colcnt, n, b.colptr, s);
+  cudaMemsetAsync(b.colcnt, 0, sizeof(int32_t) * (n + 1), s);
+  k5_fill<<<unsigned((ng * kWarp + T - 1) / T), T, 0, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.rnorm,
+                                                           nq, n, b.colptr, b.colcnt, b.csc_row, b.csc_val, status);
+  RankArgs A;
+  A.start = b.start[src];
+  A.len = b.len[src];
+  A.col = b.col[src];
+  A.val = b.val[src];
+  A.rn = b.rnorm;
+  A.colptr = b.colptr;
+  A.csc_row = b.csc_row;
+  A.csc_val = b.csc_val;
+  A.nq = nq;
+  A.ng = ng;
+  A.topk = sh.topk;
+  A.out_idx = out_idx;
+  A.out_dist = out_dist;
+  A.gscratch = b.rank_scratch;
+  const size_t smem = rank_smem_bytes(ng, RT);
+  A.acc_smem = smem > rank_smem_fixed(ng);
+  A.status = status;
+  cudaFuncSetAttribute(k6_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  k6_rank<<<sh.rank_ctas, RT, smem, s>>>(A);
+  return 4;
+}
+
+int rank_threads() { return RT; }
+
+}  // namespace rr
