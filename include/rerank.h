@@ -118,6 +118,34 @@ rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void
 rerank_status rerank_knn(rerank_ctx* ctx, const void* x, int64_t n, int d, int dtype, int k,
                          int32_t* out_idx, float* out_score, void* stream);
 
+/* rerank_knn without a context and without allocating anything.
+ *
+ * The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory: code running inside a framework whose memory
+ * pool owns the whole GPU, real-time loops that cannot afford an allocation,
+ * and code that must not grow its footprint at run time.  Instead of a
+ * workspace, it uses one fixed scratch area compiled into the library
+ * (RERANK_KNN_NOALLOC_SCRATCH_BYTES = 13 MiB) that every GPU which loads the
+ * library keeps until the process exits.
+ *
+ *   x, out_idx, out_score, n, d, dtype, k: as rerank_knn, but all three buffers
+ *   must be device memory (EINVAL otherwise).
+ * Limits: n <= RERANK_KNN_NOALLOC_MAX_N, d <= RERANK_KNN_NOALLOC_MAX_D,
+ * k <= RERANK_KNN_NOALLOC_MAX_K; larger sizes return EBUDGET and nothing runs.
+ * The first call on a device looks up the scratch area's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one scratch area: two calls whose work overlaps on the
+ * GPU (for instance on two streams, or from two host threads) race and give
+ * wrong results.  Calls on one stream, one after another, are safe.  The call
+ * returns after a stream synchronisation, with the status of the device work.
+ * Errors: EINVAL, EBUDGET, ECUDA, EINTERNAL as for rerank_knn. */
+#define RERANK_KNN_NOALLOC_SCRATCH_BYTES (13u << 20)
+#define RERANK_KNN_NOALLOC_MAX_N 4096
+#define RERANK_KNN_NOALLOC_MAX_D 256
+#define RERANK_KNN_NOALLOC_MAX_K 64
+rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int dtype, int k, int32_t* out_idx,
+                                 float* out_score, void* stream);
+
 /* Counters of the last rerank_run / rerank_knn call on this context. */
 typedef struct {
   int64_t n_vertices;
