@@ -179,7 +179,10 @@ enum {
   RERANK_DBG_HL_START = 5,   /* n int64: row start of h^(L) in the padded CSR */
   RERANK_DBG_HL_LEN = 6,     /* n int32: row length of h^(L) */
   RERANK_DBG_HL_COL = 7,     /* capacity int32 (read rows through START/LEN) */
-  RERANK_DBG_HL_VAL = 8      /* capacity float */
+  RERANK_DBG_HL_VAL = 8,     /* capacity float */
+  RERANK_DBG_PART_S = 9,     /* n x P x K float: per-chunk candidate scores of the similarity kernel */
+  RERANK_DBG_PART_I = 10,    /* n x P x K int32: their column indices (0x7fffffff = empty slot) */
+  RERANK_DBG_QERR = 11       /* n_pad float: per-row bound on ||unit row - its BF16/FP8 copy|| (tensor-core path) */
 };
 rerank_status rerank_debug_copy(const rerank_ctx* ctx, int what, void* dst, size_t cap,
                                 size_t* bytes);

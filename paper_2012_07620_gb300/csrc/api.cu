@@ -85,8 +85,12 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
     b.out_dist = c.take<float>(size_t(sh.nq) * (sh.knn_only ? k1 : sh.topk));
   }
   b.xhat = c.take<float>(size_t(np) * sh.dp);
-  b.xlow = precision == RERANK_PREC_FP32 ? nullptr : c.take<char>(size_t(np) * sh.dp * 2);
+  b.xlow = precision == RERANK_PREC_FP32
+               ? nullptr
+               : c.take<char>(size_t(np) * sh.dp * (precision == RERANK_PREC_FP8 ? 1 : 2));
   b.xscale = c.take<float>(size_t(np));
+  b.qerr = c.take<float>(size_t(np));
+  b.qerr_max = c.take<float>(4);
   b.norm = c.take<double>(size_t(np));
   b.part_s = c.take<float>(size_t(n) * sh.P * sh.K);
   b.part_i = c.take<int32_t>(size_t(n) * sh.P * sh.K);
@@ -196,12 +200,31 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
     dg = b.xg;
     tm.mark("h2d");
   }
-  nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xscale, ctx->cfg.precision, ctx->d_status, s);
+  const int prec = ctx->cfg.precision;
+  nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xscale, b.qerr, b.qerr_max, prec, ctx->d_status, s);
   tm.mark("normalize");
-  nl += launch_sim_fp32_topk(sh, b.xhat, b.part_s, b.part_i, ctx->sm_count, s);
+  double eps_g;
+  const float* qerr = nullptr;
+  const float* qerr_max = nullptr;
+  if (prec == RERANK_PREC_FP32) {
+    nl += launch_sim_fp32_topk(sh, b.xhat, b.part_s, b.part_i, ctx->sm_count, s);
+    // One FMA chain of dp terms over unit rows.
+    eps_g = (sh.dp + 10) * kU32 * 1.01;
+  } else {
+    const int r = launch_sim_tc_topk(sh, b.xlow, prec == RERANK_PREC_FP8, b.xscale, b.part_s, b.part_i,
+                                     ctx->d_status, ctx->sm_count, s);
+    if (r < 0) return RERANK_ECUDA;
+    nl += r;
+    // Quantisation error enters per row (qerr); on top: the FP32 accumulation of
+    // dp/16 (BF16) or dp/32 (FP8) tensor-core partial sums, each charged 2u, the
+    // rounding of the unit rows (4u) and of the FP8 scale products (2u).
+    eps_g = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
+    qerr = b.qerr;
+    qerr_max = b.qerr_max;
+  }
   tm.mark("similarity_topk");
-  const double eps_g = (sh.dp + 10) * kU32 * 1.01;
-  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, eps_g, b.knn_idx, b.knn_score, b.fb_rows,
+  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, eps_g, qerr, qerr_max, b.knn_idx, b.knn_score,
+                      b.fb_rows,
                 b.fb_count, ctx->d_status, s);
   float* fb_s = reinterpret_cast<float*>(b.scan_tmp);
   int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(ctx->sm_count) * fallback_warps() * sh.K);
@@ -269,9 +292,12 @@ rerank_status plan(rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, in
   sh.nq = nq;
   sh.ng = ng;
   sh.n = nq + ng;
-  sh.np = round_up(sh.n, 128);
+  const int prec = ctx->cfg.precision;
+  const bool tc = prec != RERANK_PREC_FP32;
+  // Tensor-core tiles are 128 rows x 256 columns; FP8 k-blocks are 128 bytes = 128 elements.
+  sh.np = round_up(sh.n, tc ? 256 : 128);
   sh.d = d;
-  sh.dp = int(round_up(d, 64));
+  sh.dp = int(round_up(d, prec == RERANK_PREC_FP8 ? 128 : 64));
   sh.dtype = dtype;
   sh.k1 = k1;
   sh.k2 = k2;
@@ -280,12 +306,12 @@ rerank_status plan(rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, in
   sh.knn_only = knn_only;
   sh.host_in = host_in;
   sh.host_out = host_out;
-  const int kmax = std::min(sim_fp32_kmax(), refine_kmax());
+  const int kmax = std::min(tc ? tc_kmax() : sim_fp32_kmax(), refine_kmax());
   if (k1 > kmax) return RERANK_EUNSUPPORTED;
   int64_t K = std::min<int64_t>(int64_t(k1) + std::max(ctx->cfg.rescore_m, 0), sh.n);
   K = std::min<int64_t>(K, kmax);
   sh.K = int(K);
-  sh.P = choose_chunks(sh.np / 128, sh.np / 128, ctx->sm_count, ctx->tune.sim_chunks);
+  sh.P = choose_chunks(sh.np / 128, sh.np / (tc ? 256 : 128), ctx->sm_count, ctx->tune.sim_chunks);
   // Capacity of a propagation layer: sum over rows of ub_i <= min(n, sum_j len_j).
   // n^2 bounds it exactly for small graphs; otherwise a generous guess, grown on overflow.
   int64_t guess = std::max<int64_t>(2 * sh.n * k1, std::min<int64_t>(sh.n * sh.n, sh.n * int64_t(k2 + 1) * 160));
@@ -412,9 +438,7 @@ rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void
   if (!ctx || !xq || !xg || !out_idx || !out_dist) return RERANK_EINVAL;
   rerank_status st = rerank_check_args(nq, ng, d, dtype, k1, k2, layers, topk_out);
   if (st != RERANK_OK) return st;
-  if (ctx->cfg.aggregator == RERANK_AGG_MAX || ctx->cfg.feature_mode == RERANK_FEAT_X ||
-      ctx->cfg.precision != RERANK_PREC_FP32)
-    return RERANK_EUNSUPPORTED;
+  if (ctx->cfg.aggregator == RERANK_AGG_MAX || ctx->cfg.feature_mode == RERANK_FEAT_X) return RERANK_EUNSUPPORTED;
   RR_CUDA(cudaSetDevice(ctx->device));
   const bool host_in = is_host_ptr(xq) || is_host_ptr(xg);
   const bool host_out = is_host_ptr(out_idx) || is_host_ptr(out_dist);
@@ -429,7 +453,6 @@ rerank_status rerank_knn(rerank_ctx* ctx, const void* x, int64_t n, int d, int d
   if (!ctx || !x || !out_idx || !out_score) return RERANK_EINVAL;
   if (n < 1 || d < 1 || k < 1 || k > n || (dtype != RERANK_DTYPE_F32 && dtype != RERANK_DTYPE_BF16))
     return RERANK_EINVAL;
-  if (ctx->cfg.precision != RERANK_PREC_FP32) return RERANK_EUNSUPPORTED;
   RR_CUDA(cudaSetDevice(ctx->device));
   const bool host_in = is_host_ptr(x);
   const bool host_out = is_host_ptr(out_idx) || is_host_ptr(out_score);
@@ -473,9 +496,13 @@ rerank_status rerank_debug_copy(const rerank_ctx* ctx, int what, void* dst, size
     case RERANK_DBG_HL_LEN: src = b.len[last]; nb = size_t(sh.n) * 4; break;
     case RERANK_DBG_HL_COL: src = b.col[last]; nb = size_t(last == 2 ? 2 * sh.n * sh.k1 : sh.cap_h) * 4; break;
     case RERANK_DBG_HL_VAL: src = b.val[last]; nb = size_t(last == 2 ? 2 * sh.n * sh.k1 : sh.cap_h) * 4; break;
+    case RERANK_DBG_PART_S: src = b.part_s; nb = size_t(sh.n) * sh.P * sh.K * 4; break;
+    case RERANK_DBG_PART_I: src = b.part_i; nb = size_t(sh.n) * sh.P * sh.K * 4; break;
+    case RERANK_DBG_QERR: src = b.qerr; nb = size_t(sh.np) * 4; break;
     default: return RERANK_EINVAL;
   }
-  if (sh.knn_only && what > RERANK_DBG_KNN_SCORE) return RERANK_EINVAL;
+  if (sh.knn_only && what > RERANK_DBG_KNN_SCORE && what < RERANK_DBG_PART_S) return RERANK_EINVAL;
+  if (what == RERANK_DBG_QERR && ctx->cfg.precision == RERANK_PREC_FP32) return RERANK_EINVAL;
   *bytes = nb;
   if (!dst) return RERANK_OK;
   if (cap < nb || !src) return RERANK_EINVAL;

@@ -50,7 +50,9 @@ struct Buffers {
   // K0
   float* xhat = nullptr;         // np x dp, unit rows, zero padding
   void* xlow = nullptr;          // np x dp bf16 / fp8 copy for the tensor-core path
-  float* xscale = nullptr;       // np fp8 row scales
+  float* xscale = nullptr;       // np fp8 row scales (1 / s_i)
+  float* qerr = nullptr;         // np, bound on ||xhat_i - dequantised low-precision row||
+  float* qerr_max = nullptr;     // 1
   double* norm = nullptr;        // n, ||x_i|| in FP64 accuracy
   // K1 / K2
   float* part_s = nullptr;       // n x P x K
@@ -142,14 +144,22 @@ struct rerank_ctx {
 namespace rr {
 
 // ---- stage launchers (each enqueues on `s`; no host synchronisation) ----
-int launch_normalize(const Shape& sh, const void* xq, const void* xg, float* xhat, double* norm,
-                      void* xlow, float* xscale, int precision, long long* status, cudaStream_t s);
+int launch_normalize(const Shape& sh, const void* xq, const void* xg, float* xhat, double* norm, void* xlow,
+                     float* inv_scale, float* qerr, float* qerr_max, int precision, long long* status,
+                     cudaStream_t s);
 int launch_sim_fp32_topk(const Shape& sh, const float* xhat, float* part_s, int32_t* part_i,
                           int sm_count, cudaStream_t s);
+int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float* inv_scale, float* part_s,
+                       int32_t* part_i, long long* status, int sm_count, cudaStream_t s);
+// eps_gemm bounds |approximate score - S| for every pair; with qerr set (tensor-core path)
+// the bound of row i is qerr[i] + qerr_max + qerr[i] * qerr_max + eps_gemm.
 int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat,
                    const double* norm, const float* part_s, const int32_t* part_i, double eps_gemm,
+                   const float* qerr, const float* qerr_max,
                    int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
                    long long* status, cudaStream_t s);
+size_t tc_smem_bytes();
+int tc_kmax();
 int launch_refine_fallback(const Shape& sh, const void* xq, const void* xg, const float* xhat,
                             const double* norm, int32_t* knn_idx, float* knn_score,
                             const int32_t* fb_rows, const int32_t* fb_count, float* scratch_s,

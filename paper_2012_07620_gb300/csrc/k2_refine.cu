@@ -236,11 +236,20 @@ __device__ bool refine_warp(WarpSmem& w, int K, int64_t i, int k1, float B, doub
 
 __global__ void __launch_bounds__(WPB * kWarp)
 k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* __restrict__ part_i, int P,
-          int K, int k1, double eps_g, double eps_r, int32_t* fb_rows, int32_t* fb_count) {
+          int K, int k1, double eps_gemm, const float* __restrict__ qerr, const float* __restrict__ qerr_max,
+          double eps_r, int32_t* fb_rows, int32_t* fb_count) {
   __shared__ WarpSmem sm[WPB];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = int64_t(blockIdx.x) * WPB + wib;
   if (i >= n) return;
+  // Bound on |approximate score - S_ij| for this row and any column j:
+  // |<q_i, q_j> - <x_i, x_j>| <= e_i ||x_j|| + ||q_i|| e_j <= e_i + e_max + e_i e_max
+  // (unit rows, e = ||x - q||), plus the accumulation and rounding terms in eps_gemm.
+  double eps_g = eps_gemm;
+  if (qerr) {
+    const double ei = qerr[i], em = *qerr_max;
+    eps_g += ei + em + ei * em;
+  }
   WarpSmem& w = sm[wib];
   float B;
   const size_t base = size_t(i) * P * K;
@@ -340,11 +349,12 @@ static RowIo make_io(const Shape& sh, const void* xq, const void* xg, const floa
 double rescore_eps(int dp) { return (dp / 32 + 10) * kU32 * 1.01; }
 
 int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat, const double* norm,
-                   const float* part_s, const int32_t* part_i, double eps_gemm, int32_t* knn_idx,
-                   float* knn_score, int32_t* fb_rows, int32_t* fb_count, long long* status, cudaStream_t s) {
+                   const float* part_s, const int32_t* part_i, double eps_gemm, const float* qerr,
+                   const float* qerr_max, int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
+                   long long* status, cudaStream_t s) {
   RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
   const unsigned blocks = unsigned((sh.n + WPB - 1) / WPB);
-  k2_refine<<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, sh.P, sh.K, sh.k1, eps_gemm,
+  k2_refine<<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, sh.P, sh.K, sh.k1, eps_gemm, qerr, qerr_max,
                                            rescore_eps(sh.dp), fb_rows, fb_count);
   return 1;
 }

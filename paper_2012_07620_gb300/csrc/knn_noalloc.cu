@@ -125,9 +125,10 @@ extern "C" rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int
   (void)sms;
 
   noalloc_reset<<<1, 64, 0, s>>>(status, fb_count);
-  launch_normalize(sh, x, x, xhat, norm, nullptr, nullptr, RERANK_PREC_FP32, status, s);
+  launch_normalize(sh, x, x, xhat, norm, nullptr, nullptr, nullptr, nullptr, RERANK_PREC_FP32, status, s);
   launch_sim_fp32_topk(sh, xhat, part_s, part_i, kFbCtas, s);
-  launch_refine(sh, x, x, xhat, norm, part_s, part_i, (sh.dp + 10) * kU32 * 1.01, out_idx, out_score, fb_rows,
+  launch_refine(sh, x, x, xhat, norm, part_s, part_i, (sh.dp + 10) * kU32 * 1.01, nullptr, nullptr, out_idx,
+                out_score, fb_rows,
                 fb_count, status, s);
   launch_refine_fallback(sh, x, x, xhat, norm, out_idx, out_score, fb_rows, fb_count, fb_s, fb_i, status, kFbCtas,
                          s);

@@ -1,0 +1,79 @@
+"""Full-size workload (3,368 + 19,732 vectors, d = 2048, k1 = 26, k2 = 7, L = 2),
+in the configuration bench.py times.
+
+The oracle cannot run the whole pipeline here in seconds, so it checks a
+sample: the exact neighbour lists of 192 sampled rows (Eq. 7-8 in FP64).
+Everything else is checked by properties that hold at any size, and the
+BF16 and FP8 tensor-core paths must reproduce the FP32 path bit for bit.
+"""
+import numpy as np
+import pytest
+
+import parity
+from oracle import rerank_oracle as o
+from paper_2012_07620_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+K1, K2, L = 26, 7, 2
+
+
+@pytest.fixture(scope="module")
+def market():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_07620_gb300 import rerank
+    w = synthetic.make_workload(synthetic.MARKET_SCALE)
+    xq = torch.from_numpy(w.xq).cuda()
+    xg = torch.from_numpy(w.xg).cuda()
+    out = {}
+    for prec in ("fp32", "bf16", "fp8"):
+        with rerank.Reranker(precision=prec) as R:
+            idx, dist = R.run(xq, xg, K1, K2, L)
+            torch.cuda.synchronize()
+            n = len(w.xq) + len(w.xg)
+            out[prec] = dict(idx=idx.cpu().numpy(), dist=dist.cpu().numpy(),
+                             knn=R.debug("knn_idx").reshape(n, K1), info=R.last_info())
+    return w, out
+
+
+def test_sampled_neighbour_lists_match_oracle(market):
+    w, out = market
+    xu = np.concatenate([w.xq, w.xg])
+    rows = np.random.default_rng(0).choice(len(xu), 192, replace=False)
+    ridx, rscore = o.knn_lists(xu, K1, rows=rows)
+    xh = xu.astype(np.float64) / np.linalg.norm(xu.astype(np.float64), axis=1, keepdims=True)
+    for prec in ("fp32", "bf16", "fp8"):
+        got = out[prec]["knn"][rows]
+        bad = np.argwhere(got != ridx)
+        for r, p in bad:
+            i = rows[r]
+            s = xh[i] @ xh[got[r, p]]
+            assert abs(s - rscore[r, p]) <= parity.KNN_TIE, (prec, i, p)
+
+
+def test_lowprec_paths_reproduce_fp32(market):
+    _, out = market
+    for prec in ("bf16", "fp8"):
+        assert (out[prec]["knn"] == out["fp32"]["knn"]).all(), prec
+        assert (out[prec]["idx"] == out["fp32"]["idx"]).all(), prec
+        assert (out[prec]["dist"] == out["fp32"]["dist"]).all(), prec
+
+
+def test_graph_and_output_invariants(market):
+    w, out = market
+    knn = out["fp32"]["knn"]
+    n = knn.shape[0]
+    assert (knn[:, 0] == np.arange(n)).all()
+    assert all(len(set(r)) == K1 for r in knn[:: 97])
+    idx, dist = out["fp32"]["idx"], out["fp32"]["dist"]
+    g = len(w.xg)
+    assert idx.shape == (len(w.xq), g)
+    for q in range(0, len(w.xq), 211):
+        assert len(np.unique(idx[q])) == g
+        assert (np.diff(dist[q]) >= 0).all()
+        z = idx[q][dist[q] == 1.0]
+        assert (np.diff(z) > 0).all()
+    assert dist.min() >= 0.0 and dist.max() <= 1.0
