@@ -275,6 +275,7 @@ def run_ours(args, world, rank, local):
     info = R.last_info()
     line["fp64_rescored"] = info["fp64_rescored"]
     line["fallback_rows"] = info["fallback_rows"]
+    line["exact_scan_rows"] = info["exact_scan_rows"]
     if rank == 0 and not args.no_cpu_baseline:
         v, sample, threads = cpu_oracle_sample(w.xq, w.xg, k1, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": threads, "kind": "oracle", "sample": sample}

@@ -151,7 +151,8 @@ typedef struct {
   int64_t n_vertices;
   int64_t candidates_per_row;  /* K = min(k1 + rescore_m, n) */
   int64_t fp64_rescored;       /* candidate scores recomputed in FP64 near a tie */
-  int64_t fallback_rows;       /* rows whose candidate list could not be certified and were redone exactly */
+  int64_t fallback_rows;       /* rows whose first candidate list could not be certified */
+  int64_t exact_scan_rows;     /* rows finally redone by the exact FP32 scan of all columns */
   int64_t h_nnz[9];            /* nnz of h^(0) .. h^(min(L,8)) */
   int64_t workspace_bytes;     /* device workspace held by the context */
   int64_t kernel_launches;     /* kernels of this library launched by the call (last attempt) */

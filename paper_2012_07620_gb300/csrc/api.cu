@@ -89,8 +89,21 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
                ? nullptr
                : c.take<char>(size_t(np) * sh.dp * (precision == RERANK_PREC_FP8 ? 1 : 2));
   b.xscale = c.take<float>(size_t(np));
-  b.qerr = c.take<float>(size_t(np));
-  b.qerr_max = c.take<float>(4);
+  b.err = c.take<float>(3 * size_t(np));
+  b.emax = c.take<float>(4);
+  if (precision != RERANK_PREC_FP32) {
+    b.xhi = precision == RERANK_PREC_BF16 ? static_cast<__nv_bfloat16*>(b.xlow)
+                                          : c.take<__nv_bfloat16>(size_t(np) * sh.dp);
+    b.xlo = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
+    b.ahi = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
+    b.alo = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
+    b.part3_s = c.take<float>(size_t(n) * sh.P3 * sh.K);
+    b.part3_i = c.take<int32_t>(size_t(n) * sh.P3 * sh.K);
+    b.row_floor3 = c.take<int>(size_t(n));
+    b.fb2_rows = c.take<int32_t>(size_t(n));
+    b.fb2_count = c.take<int32_t>(4);
+  }
+  b.row_floor = c.take<int>(size_t(n));
   b.norm = c.take<double>(size_t(np));
   b.part_s = c.take<float>(size_t(n) * sh.P * sh.K);
   b.part_i = c.take<int32_t>(size_t(n) * sh.P * sh.K);
@@ -190,6 +203,7 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
   int64_t nl = 1;
   k_status_reset<<<1, 64, 0, s>>>(ctx->d_status);
   RR_CUDA(cudaMemsetAsync(b.fb_count, 0, sizeof(int32_t), s));
+  if (b.fb2_count) RR_CUDA(cudaMemsetAsync(b.fb2_count, 0, sizeof(int32_t), s));
   const void* dq = xq;
   const void* dg = xg;
   if (sh.host_in) {
@@ -201,36 +215,58 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
     tm.mark("h2d");
   }
   const int prec = ctx->cfg.precision;
-  nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xscale, b.qerr, b.qerr_max, prec, ctx->d_status, s);
+  nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xhi, b.xlo, b.xscale, b.err, b.emax, prec,
+                         ctx->d_status, s);
   tm.mark("normalize");
-  double eps_g;
-  const float* qerr = nullptr;
-  const float* qerr_max = nullptr;
+  ErrModel em;
+  em.err = b.err;
+  em.emax = b.emax;
+  em.np = sh.np;
   if (prec == RERANK_PREC_FP32) {
-    nl += launch_sim_fp32_topk(sh, b.xhat, b.part_s, b.part_i, ctx->sm_count, s);
+    nl += launch_sim_fp32_topk(sh, b.xhat, b.row_floor, b.part_s, b.part_i, ctx->sm_count, s);
     // One FMA chain of dp terms over unit rows.
-    eps_g = (sh.dp + 10) * kU32 * 1.01;
+    em.kind = 0;
+    em.eps = (sh.dp + 10) * kU32 * 1.01;
   } else {
-    const int r = launch_sim_tc_topk(sh, b.xlow, prec == RERANK_PREC_FP8, b.xscale, b.part_s, b.part_i,
+    const int r = launch_sim_tc_topk(sh, b.xlow, prec == RERANK_PREC_FP8, b.xscale, b.row_floor, b.part_s, b.part_i,
                                      ctx->d_status, ctx->sm_count, s);
     if (r < 0) return RERANK_ECUDA;
     nl += r;
-    // Quantisation error enters per row (qerr); on top: the FP32 accumulation of
-    // dp/16 (BF16) or dp/32 (FP8) tensor-core partial sums, each charged 2u, the
+    // Quantisation error enters per row; on top: the FP32 accumulation of dp/16
+    // (BF16) or dp/32 (FP8) tensor-core partial sums, each charged 2u, the
     // rounding of the unit rows (4u) and of the FP8 scale products (2u).
-    eps_g = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
-    qerr = b.qerr;
-    qerr_max = b.qerr_max;
+    em.kind = 1;
+    em.eps = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
   }
   tm.mark("similarity_topk");
-  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, eps_g, qerr, qerr_max, b.knn_idx, b.knn_score,
-                      b.fb_rows,
-                b.fb_count, ctx->d_status, s);
+  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, sh.P, em, nullptr, nullptr, b.knn_idx,
+                      b.knn_score, b.fb_rows, b.fb_count, ctx->d_status, s);
+  tm.mark("refine");
+  const int32_t* exact_rows = b.fb_rows;
+  const int32_t* exact_count = b.fb_count;
+  if (prec != RERANK_PREC_FP32) {
+    // Recheck the uncertified rows with the hi/lo split on the tensor cores:
+    // |S' - S| is ~1e-5 instead of ~1e-3, enough for rows whose k1-th
+    // neighbour sits among many near-equal scores.
+    nl += launch_gather_rows(b.fb_rows, b.fb_count, b.xhi, b.xlo, b.ahi, b.alo, sh.n, sh.dp, s);
+    const int r = launch_sim_tc_split_topk(sh, sh.P3, b.ahi, b.alo, b.xhi, b.xlo, b.fb_rows, b.fb_count,
+                                           b.row_floor3, b.part3_s, b.part3_i, ctx->d_status, ctx->sm_count, s);
+    if (r < 0) return RERANK_ECUDA;
+    nl += r;
+    ErrModel e3 = em;
+    e3.kind = 2;
+    e3.eps = (3 * (sh.dp / 16) + 32) * 2.0 * kU32 + 8.0 * kU32;
+    nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3, e3, b.fb_rows, b.fb_count,
+                        b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, ctx->d_status, s);
+    exact_rows = b.fb2_rows;
+    exact_count = b.fb2_count;
+    tm.mark("recheck");
+  }
   float* fb_s = reinterpret_cast<float*>(b.scan_tmp);
   int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(ctx->sm_count) * fallback_warps() * sh.K);
-  nl += launch_refine_fallback(sh, dq, dg, b.xhat, b.norm, b.knn_idx, b.knn_score, b.fb_rows, b.fb_count, fb_s, fb_i,
-                         ctx->d_status, ctx->sm_count, s);
-  tm.mark("refine");
+  nl += launch_refine_fallback(sh, dq, dg, b.xhat, b.norm, b.knn_idx, b.knn_score, exact_rows, exact_count, fb_s, fb_i,
+                               ctx->d_status, ctx->sm_count, s);
+  tm.mark("exact_scan");
   if (sh.knn_only) {
     const size_t bytes = size_t(sh.n) * sh.k1;
     int32_t* oi = sh.host_out ? b.out_idx : out_idx;
@@ -273,6 +309,7 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
   const long long* h = ctx->h_status;
   ctx->info.fp64_rescored = h[kStFp64];
   ctx->info.fallback_rows = h[kStFallback];
+  ctx->info.exact_scan_rows = ctx->cfg.precision == RERANK_PREC_FP32 ? h[kStFallback] : h[kStFallback2];
   ctx->info.error_bits = int32_t(h[kStErr]);
   ctx->info.bad_row = h[kStBadRow] == LLONG_MAX ? -1 : int32_t(h[kStBadRow]);
   const int e = int(h[kStErr]);
@@ -312,6 +349,8 @@ rerank_status plan(rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, in
   K = std::min<int64_t>(K, kmax);
   sh.K = int(K);
   sh.P = choose_chunks(sh.np / 128, sh.np / (tc ? 256 : 128), ctx->sm_count, ctx->tune.sim_chunks);
+  // The recheck covers an unknown, usually small, set of rows: many short chunks keep every SM busy.
+  sh.P3 = int(std::min<int64_t>(32, sh.np / 256));
   // Capacity of a propagation layer: sum over rows of ub_i <= min(n, sum_j len_j).
   // n^2 bounds it exactly for small graphs; otherwise a generous guess, grown on overflow.
   int64_t guess = std::max<int64_t>(2 * sh.n * k1, std::min<int64_t>(sh.n * sh.n, sh.n * int64_t(k2 + 1) * 160));
@@ -498,7 +537,7 @@ rerank_status rerank_debug_copy(const rerank_ctx* ctx, int what, void* dst, size
     case RERANK_DBG_HL_VAL: src = b.val[last]; nb = size_t(last == 2 ? 2 * sh.n * sh.k1 : sh.cap_h) * 4; break;
     case RERANK_DBG_PART_S: src = b.part_s; nb = size_t(sh.n) * sh.P * sh.K * 4; break;
     case RERANK_DBG_PART_I: src = b.part_i; nb = size_t(sh.n) * sh.P * sh.K * 4; break;
-    case RERANK_DBG_QERR: src = b.qerr; nb = size_t(sh.np) * 4; break;
+    case RERANK_DBG_QERR: src = b.err; nb = size_t(sh.np) * 4; break;
     default: return RERANK_EINVAL;
   }
   if (sh.knn_only && what > RERANK_DBG_KNN_SCORE && what < RERANK_DBG_PART_S) return RERANK_EINVAL;

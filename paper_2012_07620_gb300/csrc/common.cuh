@@ -26,7 +26,8 @@ enum : int {
   kStErr = 0,          // error bits (int)
   kStBadRow = 1,       // first offending input row
   kStFp64 = 2,         // candidates rescored in FP64
-  kStFallback = 3,     // rows sent to the exact full-row fallback
+  kStFallback = 3,     // rows whose first candidate list was not certified
+  kStFallback2 = 5,    // rows that needed the exact full-row scan
   kStNeed = 4,         // capacity needed by the stage that overflowed (elements)
   kStNnz0 = 8,         // nnz of h^(l) at kStNnz0 + l, l <= 8
   kStCount = 32

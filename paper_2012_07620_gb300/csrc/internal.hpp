@@ -1,6 +1,7 @@
 // Host-side internals: the context, its device workspace, and the stage launchers.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -51,8 +52,19 @@ struct Buffers {
   float* xhat = nullptr;         // np x dp, unit rows, zero padding
   void* xlow = nullptr;          // np x dp bf16 / fp8 copy for the tensor-core path
   float* xscale = nullptr;       // np fp8 row scales (1 / s_i)
-  float* qerr = nullptr;         // np, bound on ||xhat_i - dequantised low-precision row||
-  float* qerr_max = nullptr;     // 1
+  __nv_bfloat16* xhi = nullptr;  // np x dp: bf16(xhat) (the same array as xlow on the BF16 path)
+  __nv_bfloat16* xlo = nullptr;  // np x dp: bf16(xhat - hi)
+  float* err = nullptr;          // 3 x np: bounds on ||xhat - xlow||, ||lo||, ||xhat - hi - lo|| per row
+  float* emax = nullptr;         // 4: their maxima
+  // recheck of uncertified rows with the hi/lo split ("BF16x3")
+  __nv_bfloat16* ahi = nullptr;  // np x dp: hi rows of the rows being rechecked, gathered
+  __nv_bfloat16* alo = nullptr;  // np x dp: lo rows, gathered
+  float* part3_s = nullptr;      // n x P3 x K
+  int32_t* part3_i = nullptr;
+  int* row_floor3 = nullptr;     // n
+  int32_t* fb2_rows = nullptr;   // n: rows left for the exact scan
+  int32_t* fb2_count = nullptr;
+  int* row_floor = nullptr;      // n, shared K-th best per row (similarity kernels)
   double* norm = nullptr;        // n, ||x_i|| in FP64 accuracy
   // K1 / K2
   float* part_s = nullptr;       // n x P x K
@@ -98,6 +110,7 @@ struct Shape {
   int64_t nq = 0, ng = 0, n = 0, np = 0;
   int d = 0, dp = 0, dtype = 0;
   int k1 = 0, k2 = 0, layers = 0, K = 0, P = 0;
+  int P3 = 0;              // column chunks of the hi/lo recheck
   int64_t topk = 0;
   bool host_in = false, host_out = false;
   bool knn_only = false;
@@ -145,17 +158,37 @@ namespace rr {
 
 // ---- stage launchers (each enqueues on `s`; no host synchronisation) ----
 int launch_normalize(const Shape& sh, const void* xq, const void* xg, float* xhat, double* norm, void* xlow,
-                     float* inv_scale, float* qerr, float* qerr_max, int precision, long long* status,
-                     cudaStream_t s);
-int launch_sim_fp32_topk(const Shape& sh, const float* xhat, float* part_s, int32_t* part_i,
-                          int sm_count, cudaStream_t s);
-int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float* inv_scale, float* part_s,
-                       int32_t* part_i, long long* status, int sm_count, cudaStream_t s);
-// eps_gemm bounds |approximate score - S| for every pair; with qerr set (tensor-core path)
-// the bound of row i is qerr[i] + qerr_max + qerr[i] * qerr_max + eps_gemm.
+                     __nv_bfloat16* xhi, __nv_bfloat16* xlo, float* inv_scale, float* err, float* emax,
+                     int precision, long long* status, cudaStream_t s);
+// Copy the hi/lo rows listed in rows[0 .. *count) to dst_hi/dst_lo[0 .. *count).
+int launch_gather_rows(const int32_t* rows, const int32_t* count, const __nv_bfloat16* hi, const __nv_bfloat16* lo,
+                       __nv_bfloat16* dst_hi, __nv_bfloat16* dst_lo, int64_t n, int dp, cudaStream_t s);
+// row_floor: n ints of scratch (reset by the launcher) through which chunks of
+// a row share their K-th best score.
+int launch_sim_fp32_topk(const Shape& sh, const float* xhat, int* row_floor, float* part_s, int32_t* part_i,
+                         int sm_count, cudaStream_t s);
+int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float* inv_scale, int* row_floor,
+                       float* part_s, int32_t* part_i, long long* status, int sm_count, cudaStream_t s);
+// hi/lo split: S' = hi_i.hi_j + lo_i.hi_j + hi_i.lo_j for the rows rows[0 .. *count)
+// (their hi/lo copies gathered in ahi/alo) against every column; lists indexed by
+// position in `rows`, P3 chunks.
+int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
+                             const __nv_bfloat16* bhi, const __nv_bfloat16* blo, const int32_t* rows,
+                             const int32_t* count, int* row_floor, float* part_s, int32_t* part_i,
+                             long long* status, int sm_count, cudaStream_t s);
+
+// Bound on |approximate score - S_ij| used to certify a row's candidate list.
+struct ErrModel {
+  int kind = 0;                  // 0: eps only; 1: one quantised copy; 2: hi/lo split
+  double eps = 0.0;              // accumulation and rounding part
+  const float* err = nullptr;    // 3 x np per-row bounds (see Buffers::err)
+  const float* emax = nullptr;
+  int64_t np = 0;
+};
+// Rows: all n, or rows[0 .. *count) when rows is set (lists then indexed by position).
 int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat,
-                   const double* norm, const float* part_s, const int32_t* part_i, double eps_gemm,
-                   const float* qerr, const float* qerr_max,
+                   const double* norm, const float* part_s, const int32_t* part_i, int P, const ErrModel& em,
+                   const int32_t* rows, const int32_t* count,
                    int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
                    long long* status, cudaStream_t s);
 size_t tc_smem_bytes();

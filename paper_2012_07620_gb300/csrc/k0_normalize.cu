@@ -1,6 +1,6 @@
 // K0: unit-normalise every vertex feature (the normalisation inside cos, Eq. 7)
-// and, for the tensor-core path, write the low-precision copy with a bound on
-// its error.
+// and, for the tensor-core path, write the low-precision copies with bounds on
+// their errors.
 //
 // One warp per row.  The squared norm is summed with the compensated "Dot2"
 // scheme of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J.
@@ -10,10 +10,13 @@
 // combines its 32 partials in double.  Outputs:
 //   xhat[i][k] = x_ik * fl32(1 / ||x_i||)   (FP32, zero padded to dp columns)
 //   norm[i]    = ||x_i||                    (double)
-//   BF16 path: xlow = bf16(xhat)
+//   BF16 path: xlow = hi = bf16(xhat)
 //   FP8 path:  xlow = e4m3(xhat * s_i) with s_i = 448 / max_k |xhat_ik|,
 //              inv_scale[i] = 1 / s_i
-//   qerr[i]    >= || xhat_i - dequantised xlow_i ||_2, and qerr_max >= max_i qerr[i]
+//   both:      hi = bf16(xhat), lo = bf16(xhat - hi); xhat = hi + lo + r
+//              exactly (each subtraction is exact in FP32)
+//   err[0][i] >= || xhat_i - dequantised xlow_i ||,  err[1][i] >= ||lo_i||,
+//   err[2][i] >= ||r_i||, and emax[0..2] >= their maxima over rows.
 // A row with a NaN/Inf element or zero norm sets an error bit and its index.
 #include <cuda_fp8.h>
 
@@ -35,28 +38,38 @@ __device__ __forceinline__ float warp_max_f(float v) {
   return v;
 }
 
-// MODE: 0 = FP32 only, 1 = also BF16, 2 = also FP8-E4M3 with a per-row scale.
+// The FP32 sum of squares is within (d/32 + 5) u of exact; round each bound up.
+__device__ __forceinline__ float bound_of(float sumsq) { return sqrtf(sumsq) * 1.0001f + 1e-30f; }
+
+// MODE: 0 = FP32 only, 1 = BF16 (xlow is hi), 2 = FP8-E4M3 with a per-row scale.
 template <int MODE>
 __global__ void __launch_bounds__(256) k0_normalize(const void* __restrict__ xq, const void* __restrict__ xg,
                                                     int64_t nq, int64_t n, int64_t np, int d, int dp, int dtype,
                                                     float* __restrict__ xhat, double* __restrict__ norm,
-                                                    void* __restrict__ xlow, float* __restrict__ inv_scale,
-                                                    float* __restrict__ qerr, float* __restrict__ qerr_max,
+                                                    void* __restrict__ xlow, __nv_bfloat16* __restrict__ xhi,
+                                                    __nv_bfloat16* __restrict__ xlo, float* __restrict__ inv_scale,
+                                                    float* __restrict__ err, float* __restrict__ emax,
                                                     long long* __restrict__ status) {
   const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= np) return;
   float* out = xhat + row * dp;
-  __nv_bfloat16* outb = MODE == 1 ? reinterpret_cast<__nv_bfloat16*>(xlow) + row * dp : nullptr;
+  __nv_bfloat16* outh = MODE != 0 ? xhi + row * dp : nullptr;
+  __nv_bfloat16* outl = MODE != 0 ? xlo + row * dp : nullptr;
   __nv_fp8_e4m3* out8 = MODE == 2 ? reinterpret_cast<__nv_fp8_e4m3*>(xlow) + row * dp : nullptr;
   auto zero_row = [&]() {
     for (int k = lane; k < dp; k += kWarp) {
       out[k] = 0.f;
-      if (MODE == 1) outb[k] = __float2bfloat16_rn(0.f);
+      if (MODE != 0) {
+        outh[k] = __float2bfloat16_rn(0.f);
+        outl[k] = __float2bfloat16_rn(0.f);
+      }
       if (MODE == 2) out8[k] = __nv_fp8_e4m3(0.f);
     }
     if (MODE != 0 && lane == 0) {
-      qerr[row] = 0.f;
+      err[row] = 0.f;
+      err[np + row] = 0.f;
+      err[2 * np + row] = 0.f;
       if (MODE == 2) inv_scale[row] = 0.f;
     }
   };
@@ -93,17 +106,29 @@ __global__ void __launch_bounds__(256) k0_normalize(const void* __restrict__ xq,
   const double nrm = sqrt(tot);
   const float r32 = float(1.0 / nrm);
   if (lane == 0) norm[row] = nrm;
-  float err = 0.f, amax = 0.f;
+  float e_lo = 0.f, e_r = 0.f, amax = 0.f;
   for (int k = lane; k < dp; k += kWarp) {
     const float v = k < d ? load_feat(src, dtype, base + k) * r32 : 0.f;
     out[k] = v;
-    if (MODE == 1) {
-      const __nv_bfloat16 b = __float2bfloat16_rn(v);
-      outb[k] = b;
-      const float dv = v - __bfloat162float(b);
-      err = fmaf(dv, dv, err);
+    if (MODE != 0) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const float dh = v - __bfloat162float(h);          // exact
+      const __nv_bfloat16 l = __float2bfloat16_rn(dh);
+      const float rr = dh - __bfloat162float(l);          // exact
+      outh[k] = h;
+      outl[k] = l;
+      e_lo = fmaf(__bfloat162float(l), __bfloat162float(l), e_lo);
+      e_r = fmaf(rr, rr, e_r);
     }
     if (MODE == 2) amax = fmaxf(amax, fabsf(v));
+  }
+  float e_main = 0.f;
+  if (MODE == 1) {
+    // xlow = hi: its error is lo + r.
+    for (int k = lane; k < dp; k += kWarp) {
+      const float dv = out[k] - __bfloat162float(outh[k]);
+      e_main = fmaf(dv, dv, e_main);
+    }
   }
   if (MODE == 2) {
     amax = warp_max_f(amax);
@@ -115,17 +140,21 @@ __global__ void __launch_bounds__(256) k0_normalize(const void* __restrict__ xq,
       const __nv_fp8_e4m3 q(v * sc);
       out8[k] = q;
       const float dv = v - float(q) * inv;
-      err = fmaf(dv, dv, err);
+      e_main = fmaf(dv, dv, e_main);
     }
     if (lane == 0) inv_scale[row] = inv;
   }
   if (MODE != 0) {
-    err = warp_sum(err);
-    // The FP32 sum of d squares is within (d/32 + 5) u of exact; round the bound up.
-    const float e = sqrtf(err) * 1.0001f + 1e-30f;
+    const float b0 = bound_of(warp_sum(e_main));
+    const float b1 = bound_of(warp_sum(e_lo));
+    const float b2 = bound_of(warp_sum(e_r));
     if (lane == 0) {
-      qerr[row] = e;
-      atomicMax(reinterpret_cast<int*>(qerr_max), __float_as_int(e));
+      err[row] = b0;
+      err[np + row] = b1;
+      err[2 * np + row] = b2;
+      atomicMax(reinterpret_cast<int*>(emax), __float_as_int(b0));
+      atomicMax(reinterpret_cast<int*>(emax) + 1, __float_as_int(b1));
+      atomicMax(reinterpret_cast<int*>(emax) + 2, __float_as_int(b2));
     }
   }
 }
@@ -133,21 +162,21 @@ __global__ void __launch_bounds__(256) k0_normalize(const void* __restrict__ xq,
 }  // namespace
 
 int launch_normalize(const Shape& sh, const void* xq, const void* xg, float* xhat, double* norm, void* xlow,
-                     float* inv_scale, float* qerr, float* qerr_max, int precision, long long* status,
-                     cudaStream_t s) {
+                     __nv_bfloat16* xhi, __nv_bfloat16* xlo, float* inv_scale, float* err, float* emax,
+                     int precision, long long* status, cudaStream_t s) {
   const int threads = 256;
   const unsigned blocks = unsigned((sh.np * kWarp + threads - 1) / threads);
   if (precision == RERANK_PREC_BF16) {
-    cudaMemsetAsync(qerr_max, 0, sizeof(float), s);
+    cudaMemsetAsync(emax, 0, 4 * sizeof(float), s);
     k0_normalize<1><<<blocks, threads, 0, s>>>(xq, xg, sh.nq, sh.n, sh.np, sh.d, sh.dp, sh.dtype, xhat, norm, xlow,
-                                               inv_scale, qerr, qerr_max, status);
+                                               xhi, xlo, inv_scale, err, emax, status);
   } else if (precision == RERANK_PREC_FP8) {
-    cudaMemsetAsync(qerr_max, 0, sizeof(float), s);
+    cudaMemsetAsync(emax, 0, 4 * sizeof(float), s);
     k0_normalize<2><<<blocks, threads, 0, s>>>(xq, xg, sh.nq, sh.n, sh.np, sh.d, sh.dp, sh.dtype, xhat, norm, xlow,
-                                               inv_scale, qerr, qerr_max, status);
+                                               xhi, xlo, inv_scale, err, emax, status);
   } else {
     k0_normalize<0><<<blocks, threads, 0, s>>>(xq, xg, sh.nq, sh.n, sh.np, sh.d, sh.dp, sh.dtype, xhat, norm,
-                                               nullptr, nullptr, nullptr, nullptr, status);
+                                               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, status);
   }
   return 1;
 }

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.hpp"
+#include "topk_heap.cuh"
 
 namespace rr {
 namespace {
@@ -39,22 +40,27 @@ struct Smem {
 
 __global__ void __launch_bounds__(NT, 1)
 k1_sgemm_topk(const float* __restrict__ x, int64_t n, int dp, int K, int P, int col_tiles,
-              float* __restrict__ part_s, int32_t* __restrict__ part_i) {
+              int* __restrict__ row_floor, float* __restrict__ part_s, int32_t* __restrict__ part_i) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  const int chunk = blockIdx.x;
-  const int64_t row0 = int64_t(blockIdx.y) * BM;
+  // Row blocks vary fastest over the grid, so a row's later chunks start after
+  // its earlier ones have published their floors.
+  const int chunk = blockIdx.y;
+  const int64_t row0 = int64_t(blockIdx.x) * BM;
   const int t_begin = int(int64_t(chunk) * col_tiles / P);
   const int t_end = int(int64_t(chunk + 1) * col_tiles / P);
 
-  for (int e = tid; e < KMAX * BM; e += NT) {
-    sm.ls[e / BM][e % BM] = -FLT_MAX;
-    sm.li[e / BM][e % BM] = kInvalidIdx;
-  }
-  float thr_s = -FLT_MAX;
-  int thr_i = kInvalidIdx;
+  // Threads 0..127 own one row each: a top-K heap over this chunk's columns.
+  const int64_t my_row = row0 + (tid & (BM - 1));
+  const bool live = tid < BM && my_row < n;
+  RowHeap<BM> heap{&sm.ls[0][0], &sm.li[0][0], tid & (BM - 1), K, 0};
+  heap.reset(K);
+  const float floor_s = live ? key_score(row_floor[my_row]) : FLT_MAX;
+  float root_s = -FLT_MAX;
+  int root_i = kInvalidIdx;
+  bool heap_full = false;
   __syncthreads();
 
   const int lr = tid >> 2;        // loader row (and lr + 64)
@@ -128,26 +134,28 @@ k1_sgemm_topk(const float* __restrict__ x, int64_t n, int dp, int K, int P, int 
     __syncthreads();
 
     if (tid < BM) {
-      const int64_t row = row0 + tid;
-      if (row < n) {
-        const int cmax = int(tmin<int64_t>(BN, n - col0));
-        for (int c = 0; c < cmax; ++c) {
-          const int col = int(col0 + c);
-          const float v = (col == row) ? 1.0f : sm.u.c[tid][c];
-          if (ranks_before(v, col, thr_s, thr_i)) {
-            int p = K - 1;
-            while (p > 0) {
-              const float ps = sm.ls[p - 1][tid];
-              const int pi = sm.li[p - 1][tid];
-              if (!ranks_before(v, col, ps, pi)) break;
-              sm.ls[p][tid] = ps;
-              sm.li[p][tid] = pi;
-              --p;
-            }
-            sm.ls[p][tid] = v;
-            sm.li[p][tid] = col;
-            thr_s = sm.ls[K - 1][tid];
-            thr_i = sm.li[K - 1][tid];
+      // Batches of 32 columns: admission test against the current root, then a
+      // warp-convergent drain that folds in one admitted column per lane per round.
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t mask = 0;
+        for (int j = 0; j < 32; ++j) {
+          const int64_t col = col0 + c0 + j;
+          const float v = (col == my_row) ? 1.0f : sm.u.c[tid][c0 + j];
+          const bool adm = live && col < n && v >= floor_s &&
+                           (!heap_full || ranks_before(v, int(col), root_s, root_i));
+          mask |= adm ? (1u << j) : 0u;
+        }
+        while (__any_sync(kFull, mask != 0u)) {
+          if (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1u;
+            const int64_t col = col0 + c0 + j;
+            heap.push((col == my_row) ? 1.0f : sm.u.c[tid][c0 + j], int(col));
+          }
+          heap_full = heap.full();
+          if (heap_full) {
+            root_s = heap.s(0);
+            root_i = heap.i(0);
           }
         }
       }
@@ -155,7 +163,12 @@ k1_sgemm_topk(const float* __restrict__ x, int64_t n, int dp, int K, int P, int 
     __syncthreads();
   }
 
-  // Write this chunk's lists: part[(row * P + chunk) * K + r].
+  // Write this chunk's list, sorted: part[(row * P + chunk) * K + r].
+  if (live) {
+    heap.sort_desc();
+    if (heap_full) atomicMax(row_floor + my_row, score_key(sm.ls[K - 1][tid]));
+  }
+  __syncthreads();
   for (int e = tid; e < BM * K; e += NT) {
     const int r = e / K, j = e % K;
     const int64_t row = row0 + r;
@@ -169,15 +182,16 @@ k1_sgemm_topk(const float* __restrict__ x, int64_t n, int dp, int K, int P, int 
 
 }  // namespace
 
-int launch_sim_fp32_topk(const Shape& sh, const float* xhat, float* part_s, int32_t* part_i,
-                          int sm_count, cudaStream_t s) {
+int launch_sim_fp32_topk(const Shape& sh, const float* xhat, int* row_floor, float* part_s, int32_t* part_i,
+                         int sm_count, cudaStream_t s) {
   (void)sm_count;
   const int col_tiles = int(sh.np / BN);
   const int row_blocks = int(sh.np / BM);
   const size_t smem = sizeof(Smem);
+  cudaMemsetAsync(row_floor, kFloorResetByte, sizeof(int) * size_t(sh.n), s);
   cudaFuncSetAttribute(k1_sgemm_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  dim3 grid(sh.P, row_blocks);
-  k1_sgemm_topk<<<grid, NT, smem, s>>>(xhat, sh.n, sh.dp, sh.K, sh.P, col_tiles, part_s, part_i);
+  dim3 grid(row_blocks, sh.P);
+  k1_sgemm_topk<<<grid, NT, smem, s>>>(xhat, sh.n, sh.dp, sh.K, sh.P, col_tiles, row_floor, part_s, part_i);
   return 1;
 }
 

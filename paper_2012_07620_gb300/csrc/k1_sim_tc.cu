@@ -4,7 +4,8 @@
 //
 // One persistent CTA per SM walks work items (row block of 128 rows, chunk of
 // 256-column tiles); items are ordered so that CTAs running together share
-// the chunk, so the column tiles they stream are L2 hits.  Roles:
+// the chunk, so the column tiles they stream are L2 hits, and so that a row's
+// later chunks run after its earlier ones (see the floors below).  Roles:
 //   warp 0 (one thread)  TMA producer: per k-block, the 128-row A slab and
 //                        the 256-row B slab (128-byte swizzle) into a
 //                        3-stage shared-memory ring;
@@ -15,17 +16,24 @@
 //   warps 2-5            epilogue: each thread owns one TMEM lane = one row,
 //                        reads its 256 scores with tcgen05.ld (32 at a time),
 //                        applies the FP8 row/column scales, sets S_ii = 1 and
-//                        keeps a sorted top-K list (S desc, index asc) in
-//                        shared memory; then releases the accumulator.
+//                        folds admitted columns into a top-K heap (see
+//                        topk_heap.cuh); then releases the accumulator.
 // The two accumulators let the MMA of tile t+1 run under the epilogue of
-// tile t.  At the end of a work item the lists are written as one partial
-// candidate list per (row, chunk), merged and certified by K2.
+// tile t.  At the end of a work item the heap is sorted and written as one
+// partial candidate list per (row, chunk), merged and certified by K2.
+//
+// Split mode (the recheck of rows whose list could not be certified): the
+// operands are the hi/lo BF16 halves of the unit rows, x = hi + lo + r, and
+// the k-loop runs three times over the feature dimension so that the one
+// accumulator collects hi_i.hi_j + lo_i.hi_j + hi_i.lo_j.  The A rows are the
+// gathered rows being rechecked; their count is read on the device.
 #include <cuda.h>
 #include <cfloat>
 
 #include "common.cuh"
 #include "internal.hpp"
 #include "tc_ptx.cuh"
+#include "topk_heap.cuh"
 
 namespace rr {
 namespace {
@@ -39,11 +47,14 @@ constexpr int KLIST = 64;
 constexpr int THREADS = 192;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
+enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2 };
+
 struct alignas(1024) TcSmem {
   uint8_t a[STAGES][A_BYTES];
   uint8_t b[STAGES][B_BYTES];
-  float ls[KLIST][TBM];
+  float ls[KLIST][TBM];   // per-row heaps (topk_heap.cuh)
   int li[KLIST][TBM];
+  float batch[32][TBM];   // scores of the 32 columns being folded in
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
   uint64_t tfull[2];
@@ -54,28 +65,39 @@ struct alignas(1024) TcSmem {
 };
 
 struct TcArgs {
-  int64_t n;
-  int row_blocks, col_tiles, chunks, kblocks, K;
-  const float* inv_scale;  // FP8 only: 1 / s_i per row
+  int64_t n;                // columns (and rows, outside split mode)
+  int row_blocks;           // outside split mode
+  int col_tiles, chunks, kblocks, K;
+  const float* inv_scale;   // FP8 only: 1 / s_i per row
+  const int32_t* rows;      // split mode: global row of each A row
+  const int32_t* count;     // split mode: number of A rows
+  int* row_floor;           // per A row: score_key of the best K-th score any finished chunk found
   float* part_s;
   int32_t* part_i;
   long long* status;
 };
 
-__device__ __forceinline__ void item_range(const TcArgs& A, int item, int& rb, int& chunk, int& t0, int& t1) {
-  rb = item % A.row_blocks;
-  chunk = item / A.row_blocks;
+__device__ __forceinline__ void item_range(const TcArgs& A, int row_blocks, int item, int& rb, int& chunk, int& t0,
+                                           int& t1) {
+  rb = item % row_blocks;
+  chunk = item / row_blocks;
   t0 = int(int64_t(chunk) * A.col_tiles / A.chunks);
   t1 = int(int64_t(chunk + 1) * A.col_tiles / A.chunks);
 }
 
-template <bool FP8>
-__global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__ CUtensorMap tmap, TcArgs A) {
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+           const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs A) {
   extern __shared__ uint8_t smem_raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort = &sm.abort;
-  const int items = A.row_blocks * A.chunks;
+  constexpr int SEGS = MODE == MODE_SPLIT ? 3 : 1;
+  const int64_t nrows = MODE == MODE_SPLIT ? int64_t(*A.count) : A.n;
+  const int row_blocks = MODE == MODE_SPLIT ? int((nrows + TBM - 1) / TBM) : A.row_blocks;
+  const int items = row_blocks * A.chunks;
+  const int kb_total = A.kblocks * SEGS;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -89,7 +111,12 @@ __global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__
     tc::mbar_init(&sm.done, 1);
     sm.abort = 0;
     tc::fence_barrier_init();
-    tc::tma_prefetch_desc(&tmap);
+    tc::tma_prefetch_desc(&mA0);
+    tc::tma_prefetch_desc(&mB0);
+    if (MODE == MODE_SPLIT) {
+      tc::tma_prefetch_desc(&mA1);
+      tc::tma_prefetch_desc(&mB1);
+    }
   }
   if (warp == 1) {
     tc::tmem_alloc(&sm.tmem_base, 512);
@@ -109,18 +136,21 @@ __global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__
       bool ok = true;
       for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
         int rb, chunk, t0, t1;
-        item_range(A, item, rb, chunk, t0, t1);
+        item_range(A, row_blocks, item, rb, chunk, t0, t1);
         for (int ct = t0; ct < t1 && ok; ++ct) {
-          for (int kb = 0; kb < A.kblocks; ++kb) {
+          for (int kt = 0; kt < kb_total; ++kt) {
             if (!tc::mbar_wait(&sm.empty[stage], phase ^ 1u, abort, WAIT_LIMIT)) {
               ok = false;
               break;
             }
+            const int seg = kt / A.kblocks, kb = kt - seg * A.kblocks;
+            const CUtensorMap* ma = seg == 1 ? &mA1 : &mA0;
+            const CUtensorMap* mb = seg == 2 ? &mB1 : &mB0;
             tc::mbar_arrive_expect_tx(&sm.full[stage], A_BYTES + B_BYTES);
-            const int kx = kb * (FP8 ? 128 : 64);
-            tc::tma_load_2d(sm.a[stage], &tmap, &sm.full[stage], kx, rb * TBM);
-            tc::tma_load_2d(sm.b[stage], &tmap, &sm.full[stage], kx, ct * TBN);
-            tc::tma_load_2d(sm.b[stage] + B_BYTES / 2, &tmap, &sm.full[stage], kx, ct * TBN + TBN / 2);
+            const int kx = kb * (MODE == MODE_FP8 ? 128 : 64);
+            tc::tma_load_2d(sm.a[stage], ma, &sm.full[stage], kx, rb * TBM);
+            tc::tma_load_2d(sm.b[stage], mb, &sm.full[stage], kx, ct * TBN);
+            tc::tma_load_2d(sm.b[stage] + B_BYTES / 2, mb, &sm.full[stage], kx, ct * TBN + TBN / 2);
             armed |= 1u << stage;
             armed_phase = (armed_phase & ~(1u << stage)) | (phase << stage);
             if (++stage == STAGES) {
@@ -141,12 +171,12 @@ __global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = tc::instr_desc(FP8 ? 0u : 1u, TBM, TBN);
+      constexpr uint32_t idesc = tc::instr_desc(MODE == MODE_FP8 ? 0u : 1u, TBM, TBN);
       uint32_t stage = 0, phase = 0, tcount = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
         int rb, chunk, t0, t1;
-        item_range(A, item, rb, chunk, t0, t1);
+        item_range(A, row_blocks, item, rb, chunk, t0, t1);
         for (int ct = t0; ct < t1 && ok; ++ct) {
           const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
           if (!tc::mbar_wait(&sm.tempty[ab], tph ^ 1u, abort, WAIT_LIMIT)) {
@@ -155,7 +185,7 @@ __global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__
           }
           tc::tc_fence_after();
           const uint32_t d = tmem + ab * TBN;
-          for (int kb = 0; kb < A.kblocks; ++kb) {
+          for (int kt = 0; kt < kb_total; ++kt) {
             if (!tc::mbar_wait(&sm.full[stage], phase, abort, WAIT_LIMIT)) {
               ok = false;
               break;
@@ -166,10 +196,10 @@ __global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               // 32 bytes of K per instruction: advance the start address by 2 (16-byte units).
-              if (FP8)
-                tc::mma_fp8(d, da + 2u * kk, db + 2u * kk, idesc, (kb | kk) != 0);
+              if (MODE == MODE_FP8)
+                tc::mma_fp8(d, da + 2u * kk, db + 2u * kk, idesc, (kt | kk) != 0);
               else
-                tc::mma_bf16(d, da + 2u * kk, db + 2u * kk, idesc, (kb | kk) != 0);
+                tc::mma_bf16(d, da + 2u * kk, db + 2u * kk, idesc, (kt | kk) != 0);
             }
             tc::mma_commit(&sm.empty[stage]);
             if (++stage == STAGES) {
@@ -199,16 +229,19 @@ __global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__
     bool ok = true;
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
       int rb, chunk, t0, t1;
-      item_range(A, item, rb, chunk, t0, t1);
-      const int64_t grow = int64_t(rb) * TBM + r;
-      const bool live = grow < A.n;
-      for (int j = 0; j < A.K; ++j) {
-        sm.ls[j][r] = -FLT_MAX;
-        sm.li[j][r] = kInvalidIdx;
-      }
-      float thr_s = -FLT_MAX;
-      int thr_i = kInvalidIdx;
-      const float rinv = (FP8 && live) ? A.inv_scale[grow] : 1.0f;
+      item_range(A, row_blocks, item, rb, chunk, t0, t1);
+      const int64_t arow = int64_t(rb) * TBM + r;   // row of the A operand
+      const bool live = arow < nrows;
+      const int64_t grow = MODE == MODE_SPLIT ? (live ? int64_t(A.rows[arow]) : -1) : arow;  // vertex
+      RowHeap<TBM> heap{&sm.ls[0][0], &sm.li[0][0], r, A.K, 0};
+      heap.reset(A.K);
+      // Admission threshold: the heap root once the heap is full, and never
+      // below the floor left by chunks of this row that finished earlier.
+      const float floor_s = live ? key_score(A.row_floor[arow]) : FLT_MAX;
+      float root_s = -FLT_MAX;
+      int root_i = kInvalidIdx;
+      bool heap_full = false;
+      const float rinv = (MODE == MODE_FP8 && live) ? A.inv_scale[grow] : 1.0f;
       for (int ct = t0; ct < t1; ++ct) {
         const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
         if (!tc::mbar_wait(&sm.tfull[ab], tph, abort, WAIT_LIMIT)) {
@@ -220,30 +253,32 @@ __global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__
           uint32_t v[32];
           tc::tmem_ld32(tlane + ab * TBN + cb * 32, v);
           tc::tmem_wait_ld();
-          if (live) {
-            const int64_t cbase = int64_t(ct) * TBN + cb * 32;
+          // Admission test for the 32 columns against the current root, then
+          // a warp-convergent drain: every round each lane folds in at most
+          // one admitted column, so the warp pays per round, not per column.
+          const int64_t cbase = int64_t(ct) * TBN + cb * 32;
+          uint32_t mask = 0;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int64_t col = cbase + j;
-              if (col >= A.n) break;
-              float s = __uint_as_float(v[j]);
-              if (FP8) s = s * rinv * __ldg(A.inv_scale + col);
-              if (col == grow) s = 1.0f;
-              if (ranks_before(s, int(col), thr_s, thr_i)) {
-                int p = A.K - 1;
-                while (p > 0) {
-                  const float ps = sm.ls[p - 1][r];
-                  const int pi = sm.li[p - 1][r];
-                  if (!ranks_before(s, int(col), ps, pi)) break;
-                  sm.ls[p][r] = ps;
-                  sm.li[p][r] = pi;
-                  --p;
-                }
-                sm.ls[p][r] = s;
-                sm.li[p][r] = int(col);
-                thr_s = sm.ls[A.K - 1][r];
-                thr_i = sm.li[A.K - 1][r];
-              }
+          for (int j = 0; j < 32; ++j) {
+            const int64_t col = cbase + j;
+            float s = __uint_as_float(v[j]);
+            if (MODE == MODE_FP8) s = s * rinv * __ldg(A.inv_scale + (col < A.n ? col : 0));
+            if (col == grow) s = 1.0f;
+            sm.batch[j][r] = s;
+            const bool adm = live && col < A.n && s >= floor_s &&
+                             (!heap_full || ranks_before(s, int(col), root_s, root_i));
+            mask |= adm ? (1u << j) : 0u;
+          }
+          while (__any_sync(kFull, mask != 0u)) {
+            if (mask) {
+              const int j = __ffs(mask) - 1;
+              mask &= mask - 1u;
+              heap.push(sm.batch[j][r], int(cbase + j));
+            }
+            heap_full = heap.full();
+            if (heap_full) {
+              root_s = heap.s(0);
+              root_i = heap.i(0);
             }
           }
         }
@@ -254,11 +289,14 @@ __global__ void __launch_bounds__(THREADS, 1) k1_tc_topk(const __grid_constant__
       }
       if (!ok) break;
       if (live) {
-        const size_t o = (size_t(grow) * A.chunks + chunk) * A.K;
+        heap.sort_desc();
+        const size_t o = (size_t(arow) * A.chunks + chunk) * A.K;
         for (int j = 0; j < A.K; ++j) {
           A.part_s[o + j] = sm.ls[j][r];
           A.part_i[o + j] = sm.li[j][r];
         }
+        // This chunk's K-th best becomes a floor for the row's later chunks.
+        if (heap_full) atomicMax(A.row_floor + arow, score_key(sm.ls[A.K - 1][r]));
       }
     }
     if (!ok) {
@@ -289,6 +327,40 @@ EncodeFn get_encode() {
   return fn;
 }
 
+// Row-major rows x dp matrix, boxes of 128 rows x 128 bytes, 128-byte swizzle.
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int dp, bool fp8) {
+  EncodeFn enc = get_encode();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(dp), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(dp) * (fp8 ? 1 : 2)};
+  const cuuint32_t box[2] = {fp8 ? 128u : 64u, 128u};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE>
+void launch_mode(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
+                 const TcArgs& A, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(TcSmem) + 1024;
+  cudaFuncSetAttribute(k1_tc_topk<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  k1_tc_topk<MODE><<<grid, THREADS, smem, s>>>(a0, a1, b0, b1, A);
+}
+
+__global__ void k_gather_rows(const int32_t* __restrict__ rows, const int32_t* __restrict__ count,
+                              const uint4* __restrict__ hi, const uint4* __restrict__ lo, uint4* __restrict__ dhi,
+                              uint4* __restrict__ dlo, int64_t n, int vecs) {
+  const int64_t f = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (f >= n || f >= *count) return;
+  const int64_t src = rows[f];
+  for (int k = lane; k < vecs; k += kWarp) {
+    dhi[f * vecs + k] = hi[src * vecs + k];
+    dlo[f * vecs + k] = lo[src * vecs + k];
+  }
+}
+
 }  // namespace
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
@@ -298,20 +370,12 @@ int tc_tile_cols() { return TBN; }
 
 // Returns the number of kernels launched (1), or a negative value when the
 // tensor map cannot be encoded.
-int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float* inv_scale, float* part_s,
-                       int32_t* part_i, long long* status, int sm_count, cudaStream_t s) {
-  EncodeFn enc = get_encode();
-  if (!enc) return -1;
+int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float* inv_scale, int* row_floor,
+                       float* part_s, int32_t* part_i, long long* status, int sm_count, cudaStream_t s) {
   CUtensorMap map;
-  const cuuint64_t dims[2] = {cuuint64_t(sh.dp), cuuint64_t(sh.np)};
-  const cuuint64_t strides[1] = {cuuint64_t(sh.dp) * (fp8 ? 1 : 2)};
-  const cuuint32_t box[2] = {fp8 ? 128u : 64u, 128u};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(&map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                   const_cast<void*>(xlow), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return -1;
-  TcArgs A;
+  if (!make_map(&map, xlow, sh.np, sh.dp, fp8)) return -1;
+  cudaMemsetAsync(row_floor, kFloorResetByte, sizeof(int) * size_t(sh.n), s);
+  TcArgs A{};
   A.n = sh.n;
   A.row_blocks = int(sh.np / TBM);
   A.col_tiles = int(sh.np / TBN);
@@ -319,19 +383,51 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   A.kblocks = fp8 ? sh.dp / 128 : sh.dp / 64;
   A.K = sh.K;
   A.inv_scale = inv_scale;
+  A.row_floor = row_floor;
   A.part_s = part_s;
   A.part_i = part_i;
   A.status = status;
   const int items = A.row_blocks * A.chunks;
   const int grid = items < sm_count ? items : sm_count;
-  const size_t smem = tc_smem_bytes();
-  if (fp8) {
-    cudaFuncSetAttribute(k1_tc_topk<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    k1_tc_topk<true><<<grid, THREADS, smem, s>>>(map, A);
-  } else {
-    cudaFuncSetAttribute(k1_tc_topk<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    k1_tc_topk<false><<<grid, THREADS, smem, s>>>(map, A);
-  }
+  if (fp8)
+    launch_mode<MODE_FP8>(map, map, map, map, A, grid, s);
+  else
+    launch_mode<MODE_BF16>(map, map, map, map, A, grid, s);
+  return 1;
+}
+
+int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, const __nv_bfloat16* alo,
+                             const __nv_bfloat16* bhi, const __nv_bfloat16* blo, const int32_t* rows,
+                             const int32_t* count, int* row_floor, float* part_s, int32_t* part_i,
+                             long long* status, int sm_count, cudaStream_t s) {
+  CUtensorMap a0, a1, b0, b1;
+  if (!make_map(&a0, ahi, sh.np, sh.dp, false) || !make_map(&a1, alo, sh.np, sh.dp, false) ||
+      !make_map(&b0, bhi, sh.np, sh.dp, false) || !make_map(&b1, blo, sh.np, sh.dp, false))
+    return -1;
+  cudaMemsetAsync(row_floor, kFloorResetByte, sizeof(int) * size_t(sh.n), s);
+  TcArgs A{};
+  A.n = sh.n;
+  A.row_blocks = 0;
+  A.col_tiles = int(sh.np / TBN);
+  A.chunks = P3;
+  A.kblocks = sh.dp / 64;
+  A.K = sh.K;
+  A.rows = rows;
+  A.count = count;
+  A.row_floor = row_floor;
+  A.part_s = part_s;
+  A.part_i = part_i;
+  A.status = status;
+  launch_mode<MODE_SPLIT>(a0, a1, b0, b1, A, sm_count, s);
+  return 1;
+}
+
+int launch_gather_rows(const int32_t* rows, const int32_t* count, const __nv_bfloat16* hi, const __nv_bfloat16* lo,
+                       __nv_bfloat16* dst_hi, __nv_bfloat16* dst_lo, int64_t n, int dp, cudaStream_t s) {
+  const int T = 256;
+  k_gather_rows<<<unsigned((n * kWarp + T - 1) / T), T, 0, s>>>(
+      rows, count, reinterpret_cast<const uint4*>(hi), reinterpret_cast<const uint4*>(lo),
+      reinterpret_cast<uint4*>(dst_hi), reinterpret_cast<uint4*>(dst_lo), n, dp / 8);
   return 1;
 }
 

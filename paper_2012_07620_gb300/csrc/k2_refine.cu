@@ -91,11 +91,6 @@ __device__ __forceinline__ void dot2_fp32(const float* xi, const float* y0, cons
   r1 = warp_sum(acc1);
 }
 
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, o));
-  return v;
-}
 
 // P-way merge of sorted candidate lists src[p*K .. p*K+K) for p < P (P <= 32),
 // one list per lane.  Fills w.idx/w.g with the best K; returns the count and
@@ -139,10 +134,13 @@ __device__ int merge_lists(WarpSmem& w, const float* ls, const int32_t* li, int 
       }
     }
   }
-  float b = hi != kInvalidIdx ? hs : -FLT_MAX;
-  if (lane < P && li[lane * K + K - 1] != kInvalidIdx) b = fmaxf(b, ls[lane * K + K - 1]);
-  B = warp_max(b);
+  // Every column that is not a candidate scores at most the K-th candidate's
+  // score: it was either dropped from a full chunk list (below that list's
+  // K-th, which the merged K-th cannot undercut), skipped by a floor (another
+  // chunk's K-th, same argument) or not taken by the merge.  With fewer than K
+  // candidates nothing was dropped or skipped.
   __syncwarp();
+  B = cnt == K ? w.g[K - 1] : -FLT_MAX;
   return cnt;
 }
 
@@ -236,23 +234,29 @@ __device__ bool refine_warp(WarpSmem& w, int K, int64_t i, int k1, float B, doub
 
 __global__ void __launch_bounds__(WPB * kWarp)
 k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* __restrict__ part_i, int P,
-          int K, int k1, double eps_gemm, const float* __restrict__ qerr, const float* __restrict__ qerr_max,
-          double eps_r, int32_t* fb_rows, int32_t* fb_count) {
+          int K, int k1, ErrModel em, double eps_r, const int32_t* __restrict__ rows,
+          const int32_t* __restrict__ count, int32_t* fb_rows, int32_t* fb_count, int fb_stat) {
   __shared__ WarpSmem sm[WPB];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t i = int64_t(blockIdx.x) * WPB + wib;
-  if (i >= n) return;
-  // Bound on |approximate score - S_ij| for this row and any column j:
-  // |<q_i, q_j> - <x_i, x_j>| <= e_i ||x_j|| + ||q_i|| e_j <= e_i + e_max + e_i e_max
-  // (unit rows, e = ||x - q||), plus the accumulation and rounding terms in eps_gemm.
-  double eps_g = eps_gemm;
-  if (qerr) {
-    const double ei = qerr[i], em = *qerr_max;
-    eps_g += ei + em + ei * em;
+  const int64_t f = int64_t(blockIdx.x) * WPB + wib;  // position of the row in this launch's row set
+  if (f >= (rows ? int64_t(*count) : n)) return;
+  const int64_t i = rows ? int64_t(rows[f]) : f;
+  // Bound on |approximate score - S_ij| for this row and any column j (unit rows).
+  double eps_g = em.eps;
+  if (em.kind == 1) {
+    // one quantised copy q = x - e:  |<q_i,q_j> - <x_i,x_j>| <= e_i + e_max + e_i e_max
+    const double ei = em.err[i], emx = em.emax[0];
+    eps_g += ei + emx + ei * emx;
+  } else if (em.kind == 2) {
+    // x = hi + lo + r exactly, S' = hi.hi + lo.hi + hi.lo, so S - S' = lo_i.lo_j + r_i.x_j +
+    // (hi_i + lo_i).r_j and |S' - S| <= ||lo_i|| lo_max + ||r_i|| + r_max (with slack for ||x|| ~ 1):
+    const double li = em.err[em.np + i], lmx = em.emax[1];
+    const double ri = em.err[2 * em.np + i], rmx = em.emax[2];
+    eps_g += li * lmx + 1.0001 * (ri + rmx);
   }
   WarpSmem& w = sm[wib];
   float B;
-  const size_t base = size_t(i) * P * K;
+  const size_t base = size_t(f) * P * K;
   const int cnt = merge_lists(w, part_s + base, part_i + base, P, K, lane, B);
   if (cnt == n) B = -FLT_MAX;  // every column is a candidate
   if (cnt < k1) {
@@ -263,7 +267,7 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
   if (!ok && lane == 0) {
     const int slot = atomicAdd(fb_count, 1);
     fb_rows[slot] = int32_t(i);
-    atomicAdd(reinterpret_cast<unsigned long long*>(io.status + kStFallback), 1ull);
+    atomicAdd(reinterpret_cast<unsigned long long*>(io.status + fb_stat), 1ull);
   }
 }
 
@@ -349,13 +353,15 @@ static RowIo make_io(const Shape& sh, const void* xq, const void* xg, const floa
 double rescore_eps(int dp) { return (dp / 32 + 10) * kU32 * 1.01; }
 
 int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat, const double* norm,
-                   const float* part_s, const int32_t* part_i, double eps_gemm, const float* qerr,
-                   const float* qerr_max, int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
+                   const float* part_s, const int32_t* part_i, int P, const ErrModel& em, const int32_t* rows,
+                   const int32_t* count, int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
                    long long* status, cudaStream_t s) {
   RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
   const unsigned blocks = unsigned((sh.n + WPB - 1) / WPB);
-  k2_refine<<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, sh.P, sh.K, sh.k1, eps_gemm, qerr, qerr_max,
-                                           rescore_eps(sh.dp), fb_rows, fb_count);
+  // First pass: uncertified rows go to the recheck; a recheck's failures go to the exact scan.
+  const int stat = rows ? kStFallback2 : kStFallback;
+  k2_refine<<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em, rescore_eps(sh.dp), rows,
+                                           count, fb_rows, fb_count, stat);
   return 1;
 }
 

@@ -37,7 +37,8 @@ constexpr size_t kOffPartI = al(kOffPartS + sizeof(float) * kMaxN * kChunks * kM
 constexpr size_t kOffFbRows = al(kOffPartI + sizeof(int32_t) * kMaxN * kChunks * kMaxK);
 constexpr size_t kOffFbS = al(kOffFbRows + sizeof(int32_t) * kMaxN);
 constexpr size_t kOffFbI = al(kOffFbS + sizeof(float) * kFbCtas * kFbWarps * kMaxK);
-constexpr size_t kTotal = al(kOffFbI + sizeof(int32_t) * kFbCtas * kFbWarps * kMaxK);
+constexpr size_t kOffFloor = al(kOffFbI + sizeof(int32_t) * kFbCtas * kFbWarps * kMaxK);
+constexpr size_t kTotal = al(kOffFloor + sizeof(int32_t) * kMaxN);
 static_assert(kTotal <= RERANK_KNN_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
 
 // The scratch area.  In host code this name is only a stand-in for the
@@ -125,10 +126,13 @@ extern "C" rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int
   (void)sms;
 
   noalloc_reset<<<1, 64, 0, s>>>(status, fb_count);
-  launch_normalize(sh, x, x, xhat, norm, nullptr, nullptr, nullptr, nullptr, RERANK_PREC_FP32, status, s);
-  launch_sim_fp32_topk(sh, xhat, part_s, part_i, kFbCtas, s);
-  launch_refine(sh, x, x, xhat, norm, part_s, part_i, (sh.dp + 10) * kU32 * 1.01, nullptr, nullptr, out_idx,
-                out_score, fb_rows,
+  launch_normalize(sh, x, x, xhat, norm, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, RERANK_PREC_FP32,
+                   status, s);
+  launch_sim_fp32_topk(sh, xhat, reinterpret_cast<int*>(base + kOffFloor), part_s, part_i, kFbCtas, s);
+  ErrModel em;
+  em.kind = 0;
+  em.eps = (sh.dp + 10) * kU32 * 1.01;
+  launch_refine(sh, x, x, xhat, norm, part_s, part_i, sh.P, em, nullptr, nullptr, out_idx, out_score, fb_rows,
                 fb_count, status, s);
   launch_refine_fallback(sh, x, x, xhat, norm, out_idx, out_score, fb_rows, fb_count, fb_s, fb_i, status, kFbCtas,
                          s);

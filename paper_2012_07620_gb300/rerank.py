@@ -37,6 +37,7 @@ class RerankConfig(ctypes.Structure):
 class RerankInfo(ctypes.Structure):
     _fields_ = [("n_vertices", ctypes.c_int64), ("candidates_per_row", ctypes.c_int64),
                 ("fp64_rescored", ctypes.c_int64), ("fallback_rows", ctypes.c_int64),
+                ("exact_scan_rows", ctypes.c_int64),
                 ("h_nnz", ctypes.c_int64 * 9), ("workspace_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64),
                 ("error_bits", ctypes.c_int32), ("bad_row", ctypes.c_int32)]

@@ -36,6 +36,9 @@ def market():
             n = len(w.xq) + len(w.xg)
             out[prec] = dict(idx=idx.cpu().numpy(), dist=dist.cpu().numpy(),
                              knn=R.debug("knn_idx").reshape(n, K1), info=R.last_info())
+            if prec == "fp32":
+                out[prec].update(start=R.debug("hl_start")[:n], len=R.debug("hl_len")[:n],
+                                 col=R.debug("hl_col"))
     return w, out
 
 
@@ -68,12 +71,16 @@ def test_graph_and_output_invariants(market):
     n = knn.shape[0]
     assert (knn[:, 0] == np.arange(n)).all()
     assert all(len(set(r)) == K1 for r in knn[:: 97])
-    idx, dist = out["fp32"]["idx"], out["fp32"]["dist"]
-    g = len(w.xg)
-    assert idx.shape == (len(w.xq), g)
-    for q in range(0, len(w.xq), 211):
+    o32 = out["fp32"]
+    idx, dist = o32["idx"], o32["dist"]
+    nq, g = len(w.xq), len(w.xg)
+    assert idx.shape == (nq, g)
+    # gallery rows sharing a feature column with the query score > 0; the rest
+    # score exactly 0 and must close the list in ascending gallery order
+    colsets = [set(o32["col"][o32["start"][r]: o32["start"][r] + o32["len"][r]].tolist()) for r in range(n)]
+    for q in range(0, nq, 211):
         assert len(np.unique(idx[q])) == g
         assert (np.diff(dist[q]) >= 0).all()
-        z = idx[q][dist[q] == 1.0]
-        assert (np.diff(z) > 0).all()
+        zero = [gi for gi in range(g) if not (colsets[q] & colsets[nq + gi])]
+        assert idx[q][g - len(zero):].tolist() == zero
     assert dist.min() >= 0.0 and dist.max() <= 1.0
