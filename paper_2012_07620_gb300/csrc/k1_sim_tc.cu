@@ -8,7 +8,7 @@
 // later chunks run after its earlier ones (see the floors below).  Roles:
 //   warp 0 (one thread)  TMA producer: per k-block, the 128-row A slab and
 //                        the 256-row B slab (128-byte swizzle) into a
-//                        3-stage shared-memory ring;
+//                        4-stage shared-memory ring;
 //   warp 1 (one thread)  MMA issuer: 4 tcgen05.mma (K = 16 BF16 / 32 FP8) per
 //                        k-block into one of two 128 x 256 FP32 accumulators
 //                        in TMEM (512 columns), commit frees the ring slot;
@@ -16,10 +16,10 @@
 //   warps 2-5            epilogue: each thread owns one TMEM lane = one row,
 //                        reads its 256 scores with tcgen05.ld (32 at a time),
 //                        applies the FP8 row/column scales, sets S_ii = 1 and
-//                        folds admitted columns into a top-K heap (see
-//                        topk_heap.cuh); then releases the accumulator.
+//                        folds admitted columns into a sorted top-K list held
+//                        in registers; then releases the accumulator.
 // The two accumulators let the MMA of tile t+1 run under the epilogue of
-// tile t.  At the end of a work item the heap is sorted and written as one
+// tile t.  At the end of a work item the list is written as one
 // partial candidate list per (row, chunk), merged and certified by K2.
 //
 // Split mode (the recheck of rows whose list could not be certified): the
@@ -29,21 +29,22 @@
 // gathered rows being rechecked; their count is read on the device.
 #include <cuda.h>
 #include <cfloat>
+#include <climits>
 
 #include "common.cuh"
 #include "internal.hpp"
 #include "tc_ptx.cuh"
-#include "topk_heap.cuh"
+#include "topk_heap.cuh"  // score_key / key_score
 
 namespace rr {
 namespace {
 
 constexpr int TBM = 128;
 constexpr int TBN = 256;
-constexpr int STAGES = 3;
+constexpr int STAGES = 4;
 constexpr int A_BYTES = TBM * 128;    // one 128-byte swizzle row per operand row
 constexpr int B_BYTES = TBN * 128;
-constexpr int KLIST = 64;
+constexpr int KLIST = 64;  // largest candidate list the kernel supports
 constexpr int THREADS = 192;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
@@ -52,8 +53,6 @@ enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2 };
 struct alignas(1024) TcSmem {
   uint8_t a[STAGES][A_BYTES];
   uint8_t b[STAGES][B_BYTES];
-  float ls[KLIST][TBM];   // per-row heaps (topk_heap.cuh)
-  int li[KLIST][TBM];
   float batch[32][TBM];   // scores of the 32 columns being folded in
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
@@ -85,7 +84,12 @@ __device__ __forceinline__ void item_range(const TcArgs& A, int row_blocks, int 
   t1 = int(int64_t(chunk + 1) * A.col_tiles / A.chunks);
 }
 
-template <int MODE>
+// Packed ordering key of a (score, column) pair: larger = better.
+__device__ __forceinline__ long long pack_key(float s, int col) {
+  return (static_cast<long long>(score_key(s)) << 32) | static_cast<long long>(uint32_t(0x7FFFFFFF - col));
+}
+
+template <int MODE, int KL>
 __global__ void __launch_bounds__(THREADS, 1)
 k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
            const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs A) {
@@ -227,20 +231,21 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
     const uint32_t tlane = tmem + (uint32_t(q * 32) << 16);
     uint32_t tcount = 0;
     bool ok = true;
+    long long lk[KL];
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
       int rb, chunk, t0, t1;
       item_range(A, row_blocks, item, rb, chunk, t0, t1);
       const int64_t arow = int64_t(rb) * TBM + r;   // row of the A operand
       const bool live = arow < nrows;
       const int64_t grow = MODE == MODE_SPLIT ? (live ? int64_t(A.rows[arow]) : -1) : arow;  // vertex
-      RowHeap<TBM> heap{&sm.ls[0][0], &sm.li[0][0], r, A.K, 0};
-      heap.reset(A.K);
-      // Admission threshold: the heap root once the heap is full, and never
-      // below the floor left by chunks of this row that finished earlier.
+      // This row's best KL columns so far in registers, as packed keys
+      // (score_key << 32 | (INT_MAX - column)): a larger key is a better
+      // column (score desc, column asc).  Sorted descending; empty slots hold
+      // INT64_MIN, which every real column beats.  Admission: beat the last
+      // slot and reach the floor left by chunks of this row that finished earlier.
+#pragma unroll
+      for (int j = 0; j < KL; ++j) lk[j] = LLONG_MIN;
       const float floor_s = live ? key_score(A.row_floor[arow]) : FLT_MAX;
-      float root_s = -FLT_MAX;
-      int root_i = kInvalidIdx;
-      bool heap_full = false;
       const float rinv = (MODE == MODE_FP8 && live) ? A.inv_scale[grow] : 1.0f;
       for (int ct = t0; ct < t1; ++ct) {
         const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
@@ -249,14 +254,17 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
           break;
         }
         tc::tc_fence_after();
+#pragma unroll 1
         for (int cb = 0; cb < TBN / 32; ++cb) {
           uint32_t v[32];
           tc::tmem_ld32(tlane + ab * TBN + cb * 32, v);
           tc::tmem_wait_ld();
-          // Admission test for the 32 columns against the current root, then
-          // a warp-convergent drain: every round each lane folds in at most
-          // one admitted column, so the warp pays per round, not per column.
+          // Admission test of the 32 columns against the last slot, then a
+          // warp-convergent drain: every round each lane inserts at most one
+          // admitted column with a branch-free pass over its list, so the
+          // warp pays per round, not per column.
           const int64_t cbase = int64_t(ct) * TBN + cb * 32;
+          const long long thr = lk[KL - 1];
           uint32_t mask = 0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
@@ -265,21 +273,30 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
             if (MODE == MODE_FP8) s = s * rinv * __ldg(A.inv_scale + (col < A.n ? col : 0));
             if (col == grow) s = 1.0f;
             sm.batch[j][r] = s;
-            const bool adm = live && col < A.n && s >= floor_s &&
-                             (!heap_full || ranks_before(s, int(col), root_s, root_i));
+            const bool adm = live && col < A.n && s >= floor_s && pack_key(s, int(col)) > thr;
             mask |= adm ? (1u << j) : 0u;
           }
-          while (__any_sync(kFull, mask != 0u)) {
+          int rounds = __popc(mask);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(kFull, rounds, o));
+#pragma unroll 1
+          for (int rd = 0; rd < rounds; ++rd) {
+            long long c = LLONG_MIN;
             if (mask) {
               const int j = __ffs(mask) - 1;
               mask &= mask - 1u;
-              heap.push(sm.batch[j][r], int(cbase + j));
+              c = pack_key(sm.batch[j][r], int(cbase + j));
             }
-            heap_full = heap.full();
-            if (heap_full) {
-              root_s = heap.s(0);
-              root_i = heap.i(0);
-            }
+            // Insert c into the descending list: slot j takes c where c first
+            // beats lk[j], and lk[j-1] for every later slot.  All comparisons
+            // use the old list, so the pass has no serial dependency.
+            uint64_t beat = 0;
+#pragma unroll
+            for (int j = 0; j < KL; ++j) beat |= uint64_t(c > lk[j]) << j;
+#pragma unroll
+            for (int j = KL - 1; j > 0; --j)
+              lk[j] = ((beat >> j) & 1u) ? (((beat >> (j - 1)) & 1u) ? lk[j - 1] : c) : lk[j];
+            lk[0] = (beat & 1u) ? c : lk[0];
           }
         }
         tc::tc_fence_before();
@@ -289,14 +306,21 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       }
       if (!ok) break;
       if (live) {
-        heap.sort_desc();
         const size_t o = (size_t(arow) * A.chunks + chunk) * A.K;
-        for (int j = 0; j < A.K; ++j) {
-          A.part_s[o + j] = sm.ls[j][r];
-          A.part_i[o + j] = sm.li[j][r];
+        // The K-th best as a running minimum over the first K slots: written
+        // this way (not lk[K-1]) so that the list is never indexed dynamically
+        // and stays in registers.
+        long long kth = LLONG_MAX;
+#pragma unroll
+        for (int j = 0; j < KL; ++j) {
+          if (j < A.K) {
+            A.part_s[o + j] = lk[j] == LLONG_MIN ? -FLT_MAX : key_score(int(lk[j] >> 32));
+            A.part_i[o + j] = lk[j] == LLONG_MIN ? kInvalidIdx : int(0x7FFFFFFF - int(lk[j] & 0xFFFFFFFF));
+          }
+          if (j < A.K) kth = lk[j] < kth ? lk[j] : kth;
         }
         // This chunk's K-th best becomes a floor for the row's later chunks.
-        if (heap_full) atomicMax(A.row_floor + arow, score_key(sm.ls[A.K - 1][r]));
+        if (kth != LLONG_MIN && kth != LLONG_MAX) atomicMax(A.row_floor + arow, int(kth >> 32));
       }
     }
     if (!ok) {
@@ -340,12 +364,22 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int dp, bool fp8
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int MODE, int KL>
+void launch_kl(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
+               const TcArgs& A, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(TcSmem) + 1024;
+  cudaFuncSetAttribute(k1_tc_topk<MODE, KL>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  k1_tc_topk<MODE, KL><<<grid, THREADS, smem, s>>>(a0, a1, b0, b1, A);
+}
+
+// The per-row list lives in registers, so its length is a compile-time choice.
 template <int MODE>
 void launch_mode(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
                  const TcArgs& A, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(TcSmem) + 1024;
-  cudaFuncSetAttribute(k1_tc_topk<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  k1_tc_topk<MODE><<<grid, THREADS, smem, s>>>(a0, a1, b0, b1, A);
+  if (A.K <= 48)
+    launch_kl<MODE, 48>(a0, a1, b0, b1, A, grid, s);
+  else
+    launch_kl<MODE, KLIST>(a0, a1, b0, b1, A, grid, s);
 }
 
 __global__ void k_gather_rows(const int32_t* __restrict__ rows, const int32_t* __restrict__ count,

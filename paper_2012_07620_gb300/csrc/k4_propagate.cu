@@ -9,8 +9,9 @@
 // start_i is an exclusive scan of ub_i = sum_j len_j, an upper bound on the
 // output row, so every row can be written without a second pass.
 //
-// Rows with ub_i <= 1024 (almost all): one warp per row with a private
-// open-addressing hash table in shared memory (columns as keys).  The warp
+// Rows whose distinct columns fit three quarters of a 1024-slot table (almost
+// all): one warp per row with a private open-addressing hash table in shared
+// memory (columns as keys), 8 KB per warp so 24 warps share an SM.  The warp
 // walks the message list in order and adds c_j * val into the table, one
 // list at a time, so every output value is summed in message-list order and
 // the result does not depend on scheduling.  The occupied slots are
@@ -23,7 +24,8 @@
 namespace rr {
 namespace {
 
-constexpr int WSLOTS = 2048;  // hash slots per warp
+constexpr int WSLOTS = 1024;  // hash slots per warp (8 KB: 24 warps per SM)
+constexpr int WDIRECT = 4 * WSLOTS;  // ub above this goes straight to the CTA path
 constexpr int KEY_EMPTY = -1;
 constexpr int BIG_THREADS = 256;
 
@@ -42,7 +44,7 @@ __global__ void k4_ub(const int32_t* __restrict__ nbr, const int32_t* __restrict
   for (int q = 0; q < m; ++q) u += len[nbr[i * k2p1 + q]];
   if (u > n) u = n;
   ub[i] = int32_t(u);
-  if (u > WSLOTS / 2) big_rows[atomicAdd(big_count, 1)] = int32_t(i);
+  if (u > WDIRECT) big_rows[atomicAdd(big_count, 1)] = int32_t(i);
 }
 
 __device__ __forceinline__ bool capacity_ok(const int64_t* dstart, int64_t n, int64_t cap, long long* status) {
@@ -58,7 +60,8 @@ __device__ __forceinline__ bool capacity_ok(const int64_t* dstart, int64_t n, in
   return true;
 }
 
-__device__ __forceinline__ void hash_add(volatile int* keys, float* vals, int mask, int shift, int col, float v,
+// Adds v to the entry of `col`; returns true when this call created the entry.
+__device__ __forceinline__ bool hash_add(volatile int* keys, float* vals, int mask, int shift, int col, float v,
                                          long long* status) {
   const unsigned h = (unsigned(col) * 2654435761u) >> shift;
   for (int probe = 0; probe <= mask; ++probe) {
@@ -66,17 +69,18 @@ __device__ __forceinline__ void hash_add(volatile int* keys, float* vals, int ma
     const int k = keys[slot];
     if (k == col) {
       vals[slot] += v;
-      return;
+      return false;
     }
     if (k == KEY_EMPTY) {
       const int old = atomicCAS(const_cast<int*>(keys) + slot, KEY_EMPTY, col);
       if (old == KEY_EMPTY || old == col) {
         vals[slot] += v;
-        return;
+        return old == KEY_EMPTY;
       }
     }
   }
   set_error(status, kErrInternal);
+  return false;
 }
 
 __device__ __forceinline__ int next_pow2(int x) {
@@ -90,7 +94,8 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
              const float* __restrict__ sval, const int32_t* __restrict__ nbr, const float* __restrict__ nbr_w,
              const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ ub,
              const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen, int32_t* __restrict__ dcol,
-             float* __restrict__ dval, int64_t n, int64_t cap, long long* __restrict__ status) {
+             float* __restrict__ dval, int64_t n, int64_t cap, int32_t* __restrict__ big_rows,
+             int32_t* __restrict__ big_count, long long* __restrict__ status) {
   extern __shared__ int smem_i[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   volatile int* keys = smem_i + wib * WSLOTS * 2;
@@ -104,20 +109,41 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
   const unsigned lt = (1u << lane) - 1u;
   for (int64_t i = int64_t(blockIdx.x) * nw + wib; i < n; i += int64_t(gridDim.x) * nw) {
     const int u = ub[i];
-    if (u > WSLOTS / 2) continue;
-    const int T = next_pow2(max(64, 2 * u));
+    if (u > WDIRECT) continue;
+    // Table of at least twice the bound on distinct columns, at most WSLOTS; when
+    // the bound is larger the row is tried here and handed to the CTA path if
+    // its distinct columns fill three quarters of the table.
+    const int T = min(WSLOTS, next_pow2(max(64, 2 * u)));
     const int mask = T - 1, shift = 32 - (31 - __clz(T));
+    const int limit = (3 * T) / 4;
     const int m = nbr_n[i];
-    for (int q = 0; q < m; ++q) {
+    int distinct = 0;
+    bool spilled = false;
+    for (int q = 0; q < m && !spilled; ++q) {
       const int32_t j = nbr[i * k2p1 + q];
       const float cj = nbr_w[i * k2p1 + q];
       const int64_t a = sstart[j];
       const int lj = slen[j];
       for (int e0 = 0; e0 < lj; e0 += kWarp) {
         const int e = e0 + lane;
-        if (e < lj) hash_add(keys, vals, mask, shift, scol[a + e], cj * sval[a + e], status);
-        __syncwarp();
+        bool fresh = false;
+        if (e < lj) fresh = hash_add(keys, vals, mask, shift, scol[a + e], cj * sval[a + e], status);
+        distinct += __popc(__ballot_sync(kFull, fresh));
+        __syncwarp();  // this step's table writes are visible to the next step
+        if (distinct > limit) {
+          spilled = true;
+          break;
+        }
       }
+    }
+    if (spilled) {
+      for (int s = lane; s < T; s += kWarp) {
+        keys[s] = KEY_EMPTY;
+        vals[s] = 0.f;
+      }
+      if (lane == 0) big_rows[atomicAdd(big_count, 1)] = int32_t(i);
+      __syncwarp();
+      continue;
     }
     // Compact occupied slots to the front (order-preserving, in place).
     int cnt = 0;
@@ -286,7 +312,7 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
   const unsigned blocks = unsigned(tmin<int64_t>(blocks_needed, int64_t(sm_count) * (per_sm > 0 ? per_sm : 1)));
   k4_spmm_warp<<<blocks, warps * kWarp, smem, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                    b.nbr_n, k2p1, b.ub, b.start[dst], b.len[dst], b.col[dst],
-                                                   b.val[dst], n, sh.cap_h, status);
+                                                   b.val[dst], n, sh.cap_h, b.big_rows, b.big_count, status);
   k4_spmm_big<<<sm_count, BIG_THREADS, 0, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                b.nbr_n, k2p1, b.big_rows, b.big_count, b.start[dst], b.len[dst],
                                                b.col[dst], b.val[dst], n, sh.cap_h, b.hash_keys_vals,
