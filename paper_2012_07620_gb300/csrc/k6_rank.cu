@@ -22,7 +22,7 @@ namespace {
 
 constexpr int RT = 1024;                // threads per ranking CTA
 constexpr int RW = RT / kWarp;
-constexpr int SORT_CAP = 4096;          // non-zeros sorted in shared memory
+constexpr int SORT_CAP = 8192;          // non-zeros sorted in shared memory
 constexpr float kFix = 2147483648.0f;   // 2^31
 constexpr float kUnfix = 4.656612873077393e-10f;  // 2^-31
 
@@ -83,38 +83,45 @@ __device__ int block_exscan(int v, int* tmp, int& excl) {
   return total;
 }
 
-// Stable LSD radix sort of (key, val) ascending by key; returns the buffer pair holding the result.
+// Stable LSD radix sort of (key, val) ascending by key, four 8-bit passes.
+// Each warp owns a contiguous segment and counts its digits; the scatter
+// offsets are one exclusive scan over the (digit, warp) counts in digit-major
+// order, so equal digits keep their order across warps, and __match_any_sync
+// ranks them within a warp.  All threads of the block must call it; the
+// result ends in (keys, vals), whose pointers are swapped as passes run.
 __device__ void block_radix_sort(uint32_t*& keys, uint32_t*& vals, uint32_t*& tkeys, uint32_t*& tvals, int cnt,
-                                 uint32_t* hist, int* tmp) {
+                                 uint32_t* hist, int* tmp, int* skip) {
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int seg = (cnt + RW - 1) / RW;
   const int a = min(cnt, w * seg), b = min(cnt, a + seg);
+  // Scan ownership: thread t holds digit d = t / 4 and warps 8 (t % 4) .. + 7.
+  const int sd = t >> 2, sw = (t & 3) * 8;
   for (int shift = 0; shift < 32; shift += 8) {
     for (int e = t; e < RW * 256; e += RT) hist[e] = 0;
+    if (t == 0) *skip = 0;
     __syncthreads();
     for (int p = a + lane; p < b; p += kWarp) atomicAdd(&hist[w * 256 + ((keys[p] >> shift) & 255)], 1u);
     __syncthreads();
-    int tot = 0;
-    if (t < 256) {
-      for (int ww = 0; ww < RW; ++ww) {
-        const uint32_t c = hist[ww * 256 + t];
-        hist[ww * 256 + t] = uint32_t(tot);
-        tot += int(c);
-      }
+    uint32_t c[8];
+    int part = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      c[k] = hist[(sw + k) * 256 + sd];
+      part += int(c[k]);
     }
+    int dig = part;  // total of digit sd over all warps (4 consecutive lanes)
+    dig += __shfl_xor_sync(kFull, dig, 1);
+    dig += __shfl_xor_sync(kFull, dig, 2);
+    if ((t & 3) == 0 && dig == cnt) *skip = 1;  // one digit holds every key: nothing would move
     int base;
-    const int all = block_exscan(t < 256 ? tot : 0, tmp, base);
-    (void)all;
-    // A digit that holds every key: this pass would not move anything.
-    __shared__ int skip;
-    if (t == 0) skip = 0;
-    __syncthreads();
-    if (t < 256 && tot == cnt) skip = 1;
-    __syncthreads();
-    if (skip) continue;
-    if (t < 256)
-      for (int ww = 0; ww < RW; ++ww) hist[ww * 256 + t] += uint32_t(base);
+    block_exscan(part, tmp, base);
+    if (*skip) continue;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      hist[(sw + k) * 256 + sd] = uint32_t(base);
+      base += int(c[k]);
+    }
     __syncthreads();
     for (int p0 = a; p0 < b; p0 += kWarp) {
       const int p = p0 + lane;
@@ -160,11 +167,13 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
   extern __shared__ uint32_t sm[];
   if (A.status[kStErr] & kErrOverflow) return;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   const int64_t ng = A.ng;
   const int nwords = int((ng + 31) / 32);
   uint32_t* hist = sm;                                   // RW * 256
   int* tmp = reinterpret_cast<int*>(hist + RW * 256);    // 32
-  uint32_t* bits = reinterpret_cast<uint32_t*>(tmp + 32);  // nwords
+  int* misc = tmp + 32;                                  // 32: [0] = skip flag
+  uint32_t* bits = reinterpret_cast<uint32_t*>(misc + 32);  // nwords
   uint32_t* skeys = bits + ((nwords + 3) & ~3);          // SORT_CAP
   uint32_t* svals = skeys + SORT_CAP;                    // SORT_CAP
   uint32_t* sacc = svals + SORT_CAP;                     // ng (when acc_smem)
@@ -192,39 +201,38 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
       }
     }
     __syncthreads();
-    // Non-zero bitmap, one word per thread step.
-    for (int wd = t; wd < nwords; wd += RT) {
-      uint32_t b = 0u;
-      const int64_t g0 = int64_t(wd) * 32;
-      for (int k = 0; k < 32; ++k) {
-        const int64_t g = g0 + k;
-        if (g < ng && acc[g] != 0u) b |= 1u << k;
-      }
-      bits[wd] = b;
-    }
-    __syncthreads();
-    // Compact non-zeros in gallery order: key = ~acc (ascending = score desc), val = g.
-    const int64_t gc = (ng + RT - 1) / RT;
-    const int64_t ga = tmin<int64_t>(ng, t * gc), gb = tmin<int64_t>(ng, ga + gc);
+    // Non-zero bitmap and compaction, warp-cooperative: warp w owns words
+    // [w0, w1) (32 gallery entries each, lane = entry); the ballot of a word
+    // is its bitmap word, and the non-zeros go out in gallery order.
+    const int wpw = (nwords + RW - 1) / RW;
+    const int w0 = min(nwords, w * wpw), w1 = min(nwords, w0 + wpw);
     int mine = 0;
-    for (int64_t g = ga; g < gb; ++g) mine += acc[g] != 0u;
+    for (int wd = w0; wd < w1; ++wd) {
+      const int64_t g = int64_t(wd) * 32 + lane;
+      const unsigned bal = __ballot_sync(kFull, g < ng && acc[g] != 0u);
+      if (lane == 0) bits[wd] = bal;
+      mine += __popc(bal);
+    }
     int off;
-    const int cnt = block_exscan(mine, tmp, off);
+    const int cnt = block_exscan(lane == 0 ? mine : 0, tmp, off);  // one count per warp (lane 0)
+    off = __shfl_sync(kFull, off, 0);
     const bool small = cnt <= SORT_CAP && A.acc_smem && ng >= 2 * int64_t(cnt);
     uint32_t* k0 = small ? skeys : gk0;
     uint32_t* v0 = small ? svals : gv0;
-    for (int64_t g = ga; g < gb; ++g) {
-      const uint32_t x = acc[g];
-      if (x != 0u) {
-        k0[off] = ~x;
-        v0[off] = uint32_t(g);
-        ++off;
+    for (int wd = w0; wd < w1; ++wd) {
+      const unsigned bal = bits[wd];
+      const int64_t g = int64_t(wd) * 32 + lane;
+      if ((bal >> lane) & 1u) {
+        const int pos = off + __popc(bal & lt);
+        k0[pos] = ~acc[g];
+        v0[pos] = uint32_t(g);
       }
+      off += __popc(bal);
     }
     __syncthreads();
     uint32_t* k1 = small ? acc : gk1;
     uint32_t* v1 = small ? acc + cnt : gv1;
-    block_radix_sort(k0, v0, k1, v1, cnt, hist, tmp);
+    block_radix_sort(k0, v0, k1, v1, cnt, hist, tmp, misc);
     // Sorted non-zeros, then the zero tail in gallery order.
     const int64_t nout = tmin<int64_t>(T, cnt);
     for (int64_t p = t; p < nout; p += RT) {
@@ -233,28 +241,27 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
       A.out_dist[q * T + p] = 1.0f - s;
     }
     if (T > cnt) {
-      const int wc = (nwords + RT - 1) / RT;
-      const int wa = min(nwords, t * wc), wb = min(nwords, wa + wc);
       int z = 0;
-      for (int wd = wa; wd < wb; ++wd) {
+      for (int wd = w0; wd < w1; ++wd) {
         const int valid = int(tmin<int64_t>(32, ng - int64_t(wd) * 32));
         const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
         z += __popc(~bits[wd] & vm);
       }
       int zoff;
-      block_exscan(z, tmp, zoff);
-      int64_t pos = cnt + zoff;
-      for (int wd = wa; wd < wb && pos < T; ++wd) {
+      block_exscan(lane == 0 ? z : 0, tmp, zoff);
+      int64_t pos = cnt + __shfl_sync(kFull, zoff, 0);
+      for (int wd = w0; wd < w1 && pos < T; ++wd) {
         const int valid = int(tmin<int64_t>(32, ng - int64_t(wd) * 32));
         const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
-        uint32_t zb = ~bits[wd] & vm;
-        while (zb && pos < T) {
-          const int bit = __ffs(zb) - 1;
-          zb &= zb - 1;
-          A.out_idx[q * T + pos] = int32_t(int64_t(wd) * 32 + bit);
-          A.out_dist[q * T + pos] = 1.0f;
-          ++pos;
+        const uint32_t zb = ~bits[wd] & vm;
+        if ((zb >> lane) & 1u) {
+          const int64_t p = pos + __popc(zb & lt);
+          if (p < T) {
+            A.out_idx[q * T + p] = int32_t(int64_t(wd) * 32 + lane);
+            A.out_dist[q * T + p] = 1.0f;
+          }
         }
+        pos += __popc(zb);
       }
     }
     __syncthreads();
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
 
 size_t rank_smem_fixed(int64_t ng) {
   const int64_t nwords = (ng + 31) / 32;
-  return sizeof(uint32_t) * (RW * 256 + 32 + ((nwords + 3) & ~int64_t(3)) + 2 * SORT_CAP);
+  return sizeof(uint32_t) * (RW * 256 + 64 + ((nwords + 3) & ~int64_t(3)) + 2 * SORT_CAP);
 }
 
 }  // namespace
