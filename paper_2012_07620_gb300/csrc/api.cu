@@ -104,6 +104,12 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
     b.fb2_count = c.take<int32_t>(4);
   }
   b.row_floor = c.take<int>(size_t(n));
+  b.nb4 = c.take<int32_t>(4 * size_t(n));
+  b.label = c.take<int32_t>(size_t(n));
+  b.order = c.take<int32_t>(size_t(n));
+  b.ord_cnt = c.take<int32_t>(size_t(n) + 1);
+  b.ord_start = c.take<int32_t>(size_t(n) + 1);
+  b.ord_fill = c.take<int32_t>(size_t(n));
   b.norm = c.take<double>(size_t(np));
   b.part_s = c.take<float>(size_t(n) * sh.P * sh.K);
   b.part_i = c.take<int32_t>(size_t(n) * sh.P * sh.K);
@@ -239,7 +245,8 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
     em.eps = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
   }
   tm.mark("similarity_topk");
-  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, sh.P, em, nullptr, nullptr, b.knn_idx,
+  nl += launch_cluster_order(sh, b.part_s, b.part_i, b.nb4, b.label, b.ord_cnt, b.ord_start, b.ord_fill, b.order, s);
+  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, sh.P, em, b.order, nullptr, true, b.knn_idx,
                       b.knn_score, b.fb_rows, b.fb_count, ctx->d_status, s);
   tm.mark("refine");
   const int32_t* exact_rows = b.fb_rows;
@@ -256,7 +263,7 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
     ErrModel e3 = em;
     e3.kind = 2;
     e3.eps = (3 * (sh.dp / 16) + 32) * 2.0 * kU32 + 8.0 * kU32;
-    nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3, e3, b.fb_rows, b.fb_count,
+    nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3, e3, b.fb_rows, b.fb_count, false,
                         b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, ctx->d_status, s);
     exact_rows = b.fb2_rows;
     exact_count = b.fb2_count;

@@ -65,6 +65,12 @@ struct Buffers {
   int32_t* fb2_rows = nullptr;   // n: rows left for the exact scan
   int32_t* fb2_count = nullptr;
   int* row_floor = nullptr;      // n, shared K-th best per row (similarity kernels)
+  int32_t* nb4 = nullptr;        // 4n: best candidates per row (processing order)
+  int32_t* label = nullptr;      // n
+  int32_t* order = nullptr;      // n: rows grouped by cluster
+  int32_t* ord_cnt = nullptr;    // n + 1 scratch of the counting sort
+  int32_t* ord_start = nullptr;  // n + 1
+  int32_t* ord_fill = nullptr;   // n
   double* norm = nullptr;        // n, ||x_i|| in FP64 accuracy
   // K1 / K2
   float* part_s = nullptr;       // n x P x K
@@ -185,10 +191,11 @@ struct ErrModel {
   const float* emax = nullptr;
   int64_t np = 0;
 };
-// Rows: all n, or rows[0 .. *count) when rows is set (lists then indexed by position).
+// Rows: all n in index order; or rows[0 .. *count) (count == nullptr: n) in that order,
+// with the candidate lists indexed by row (part_by_row) or by position in `rows`.
 int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat,
                    const double* norm, const float* part_s, const int32_t* part_i, int P, const ErrModel& em,
-                   const int32_t* rows, const int32_t* count,
+                   const int32_t* rows, const int32_t* count, bool part_by_row,
                    int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
                    long long* status, cudaStream_t s);
 size_t tc_smem_bytes();
@@ -197,6 +204,9 @@ int launch_refine_fallback(const Shape& sh, const void* xq, const void* xg, cons
                             const double* norm, int32_t* knn_idx, float* knn_score,
                             const int32_t* fb_rows, const int32_t* fb_count, float* scratch_s,
                             int32_t* scratch_i, long long* status, int sm_count, cudaStream_t s);
+// Rows grouped cluster by cluster (label propagation over the best 4 candidates).
+int launch_cluster_order(const Shape& sh, const float* part_s, const int32_t* part_i, int32_t* nb, int32_t* label,
+                         int32_t* cnt, int32_t* start, int32_t* fill, int32_t* order, cudaStream_t s);
 int launch_scan(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
 int launch_scan32(const int32_t* in, int64_t n, int32_t* out, cudaStream_t s);
 int launch_graph(const Shape& sh, const Buffers& b, float alpha, int aggregator, int feature,

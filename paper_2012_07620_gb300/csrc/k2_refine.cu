@@ -235,11 +235,12 @@ __device__ bool refine_warp(WarpSmem& w, int K, int64_t i, int k1, float B, doub
 __global__ void __launch_bounds__(WPB * kWarp)
 k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* __restrict__ part_i, int P,
           int K, int k1, ErrModel em, double eps_r, const int32_t* __restrict__ rows,
-          const int32_t* __restrict__ count, int32_t* fb_rows, int32_t* fb_count, int fb_stat) {
+          const int32_t* __restrict__ count, bool part_by_row, int32_t* fb_rows, int32_t* fb_count,
+          int fb_stat) {
   __shared__ WarpSmem sm[WPB];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t f = int64_t(blockIdx.x) * WPB + wib;  // position of the row in this launch's row set
-  if (f >= (rows ? int64_t(*count) : n)) return;
+  if (f >= ((rows && count) ? int64_t(*count) : n)) return;
   const int64_t i = rows ? int64_t(rows[f]) : f;
   // Bound on |approximate score - S_ij| for this row and any column j (unit rows).
   double eps_g = em.eps;
@@ -256,7 +257,7 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
   }
   WarpSmem& w = sm[wib];
   float B;
-  const size_t base = size_t(f) * P * K;
+  const size_t base = size_t(part_by_row ? i : f) * P * K;
   const int cnt = merge_lists(w, part_s + base, part_i + base, P, K, lane, B);
   if (cnt == n) B = -FLT_MAX;  // every column is a candidate
   if (cnt < k1) {
@@ -354,14 +355,15 @@ double rescore_eps(int dp) { return (dp / 32 + 10) * kU32 * 1.01; }
 
 int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat, const double* norm,
                    const float* part_s, const int32_t* part_i, int P, const ErrModel& em, const int32_t* rows,
-                   const int32_t* count, int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
+                   const int32_t* count, bool part_by_row, int32_t* knn_idx, float* knn_score,
+                   int32_t* fb_rows, int32_t* fb_count,
                    long long* status, cudaStream_t s) {
   RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
   const unsigned blocks = unsigned((sh.n + WPB - 1) / WPB);
   // First pass: uncertified rows go to the recheck; a recheck's failures go to the exact scan.
-  const int stat = rows ? kStFallback2 : kStFallback;
+  const int stat = (rows && !part_by_row) ? kStFallback2 : kStFallback;
   k2_refine<<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em, rescore_eps(sh.dp), rows,
-                                           count, fb_rows, fb_count, stat);
+                                           count, part_by_row, fb_rows, fb_count, stat);
   return 1;
 }
 

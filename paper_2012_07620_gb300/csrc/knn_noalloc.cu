@@ -132,7 +132,7 @@ extern "C" rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int
   ErrModel em;
   em.kind = 0;
   em.eps = (sh.dp + 10) * kU32 * 1.01;
-  launch_refine(sh, x, x, xhat, norm, part_s, part_i, sh.P, em, nullptr, nullptr, out_idx, out_score, fb_rows,
+  launch_refine(sh, x, x, xhat, norm, part_s, part_i, sh.P, em, nullptr, nullptr, false, out_idx, out_score, fb_rows,
                 fb_count, status, s);
   launch_refine_fallback(sh, x, x, xhat, norm, out_idx, out_score, fb_rows, fb_count, fb_s, fb_i, status, kFbCtas,
                          s);
