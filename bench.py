@@ -36,6 +36,7 @@ WORKLOADS = {
     "market": dict(spec="MARKET_SCALE", k1=26, k2=7, layers=2),
     "large50k": dict(spec="LARGE_50K", k1=26, k2=7, layers=2),
     "tiny": dict(spec="TINY", k1=26, k2=7, layers=2),
+    "batched64": dict(spec=None, k1=0, k2=0, layers=0),
 }
 METRIC = "ms per N=23.1k re-rank (FP32 vs BF16+FP32 rescore); served p50/p99 ms; %roofline"
 
@@ -191,6 +192,89 @@ def _config(args, w):
             "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas x{args.gpus}"}
 
 
+def run_batched(args, world, rank, local):
+    """64 independent instances (N log-uniform 500-8000, d in {256, 512, 2048}, BF16 features)
+    per step through one rerank_run_batch call; beside it the same 64 as sequential rerank_run calls."""
+    import torch
+    import __graft_entry__
+    from paper_2012_07620_gb300 import rerank, synthetic
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    specs = synthetic.batched_specs()
+    jobs, host = [], []
+    for s in specs:
+        w = synthetic.make_workload(s["spec"])
+        xq = torch.from_numpy(w.xq).bfloat16()
+        xg = torch.from_numpy(w.xg).bfloat16()
+        nq, ng = xq.shape[0], xg.shape[0]
+        jobs.append(dict(xq=xq.to(dev), xg=xg.to(dev), k1=s["k1"], k2=s["k2"], layers=s["layers"],
+                         out_idx=torch.empty((nq, ng), dtype=torch.int32, device=dev),
+                         out_dist=torch.empty((nq, ng), dtype=torch.float32, device=dev)))
+        host.append(dict(xq=xq.pin_memory(), xg=xg.pin_memory(), k1=s["k1"], k2=s["k2"], layers=s["layers"],
+                         out_idx=torch.empty((nq, ng), dtype=torch.int32).pin_memory(),
+                         out_dist=torch.empty((nq, ng), dtype=torch.float32).pin_memory()))
+    flops = sum(2.0 * (j["xq"].shape[0] + j["xg"].shape[0]) ** 2 * j["xq"].shape[1] for j in jobs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    R = rerank.Reranker(device=local, precision=args.precision)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for _ in range(args.warmup):
+            fn()
+        _barrier(world)
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            flush.fill_(s & 255)
+            ev[s][0].record(stream)
+            fn()
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+        return _max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world) / args.steps
+
+    def sequential():
+        for j in jobs:
+            R.run(j["xq"], j["xg"], j["k1"], j["k2"], j["layers"], 0, j["out_idx"], j["out_dist"], stream)
+
+    with ClockSampler(local) as clocks:
+        batch_ms = timed(lambda: R.run_batch(jobs, stream))
+        launches = R.last_info()["kernel_launches"]
+    seq_ms = timed(sequential)
+    R.run_batch(host, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        R.run_batch(host, stream)
+    e2e_ms = _max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, world)
+    peaks, which = _peaks()
+    n_tot = sum(j["xq"].shape[0] + j["xg"].shape[0] for j in jobs)
+    line = {"metric": "ms per batch of 64 independent re-ranks (rerank_run_batch) vs 64 sequential rerank_run",
+            "value": batch_ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": batch_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"64 instances, N log-uniform 500-8000 (total {n_tot}), d in {{256, 512, 2048}}, "
+                                   "BF16 features, k1 20-30, k2 5-7, 1-3 layers, full ranked lists",
+                       "gemm_tflop": flops / 1e12, "l2": "flushed before every step (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / batch_ms,
+            "instances_per_s": 64.0 * world / (batch_ms * 1e-3),
+            "e2e": {"value": e2e_ms, "unit": "ms",
+                    "h2d_bytes_per_step": int(sum(h["xq"].numel() * 2 + h["xg"].numel() * 2 for h in host)),
+                    "d2h_bytes_per_step": int(sum(h["out_idx"].numel() * 8 for h in host))},
+            "gpu_launches": int(launches * args.steps), "clocks": clocks.summary(),
+            "roofline": {"bound": "tensor", "achieved": flops / (batch_ms * 1e-3) / 1e12,
+                         "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": flops / (batch_ms * 1e-3) / 1e12 / peaks["bf16_tflops"], "traffic": None,
+                         "kernel": "whole batch (GEMM flops / batch time)", "peak_source": f"{which} bf16 burst"}}
+    if rank == 0:
+        print(json.dumps(line))
+    R.close()
+
+
 def run_ours(args, world, rank, local):
     import torch
     import __graft_entry__
@@ -298,6 +382,8 @@ def main():
     world, rank, local = _dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batched64":
+        run_batched(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -109,6 +109,36 @@ rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void
                          int d, int dtype, int k1, int k2, int layers, int64_t topk_out,
                          int32_t* out_idx, float* out_dist, void* stream);
 
+/* One independent instance of Algorithm 1 for rerank_run_batch.  Fields as
+ * the arguments of rerank_run; `status` is written by the call. */
+typedef struct {
+  const void* xq;
+  int64_t nq;
+  const void* xg;
+  int64_t ng;
+  int d;
+  int dtype;
+  int k1, k2, layers;
+  int64_t topk_out;
+  int32_t* out_idx;
+  float* out_dist;
+  rerank_status status; /* out: this instance's result code */
+} rerank_job;
+
+/* Many independent instances of Algorithm 1 (each exactly as rerank_run would
+ * compute it; the paper defines one instance at a time, Sec. 3.3) in one call.
+ * The instances share one workspace block and run concurrently on the GPU:
+ * their stages are enqueued on internal streams forked from `stream` and
+ * joined back into it, largest instances first.  The call reads every
+ * instance's status with one device-to-host copy and one synchronisation;
+ * an instance whose propagation buffers overflowed is rerun alone.
+ *   jobs    array of njobs instances; inputs and outputs may be host or device
+ *           memory, as for rerank_run
+ * Returns OK when every instance succeeded, else the first failing status
+ * (each jobs[i].status holds its own).  Argument errors of any instance
+ * return EINVAL before anything runs. */
+rerank_status rerank_run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, void* stream);
+
 /* Steps 1-2 only: the exact top-k neighbour lists of every vertex of X (Eq. 7-8).
  *   x          n x d features (dtype)
  *   out_idx    n x k int32, sorted by (S desc, index asc); out_idx[i*k] == i

@@ -1,5 +1,6 @@
 // The C ABI (include/rerank.h): argument checks, workspace planning, stage
 // sequencing on the caller's stream, and the end-of-call error read-back.
+#include <algorithm>
 #include <climits>
 #include <cstdlib>
 #include <cstdio>
@@ -188,42 +189,42 @@ void finish_timing(rerank_ctx* ctx) {
   tm.names.clear();
 }
 
-// One attempt of the pipeline.  Returns OK, or the mapped device error.
-rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t* out_idx, float* out_dist,
-                       cudaStream_t s) {
-  Shape& sh = ctx->shape;
+// One pipeline instance: its shape, its buffers and its device status block.
+struct JobRun {
+  Shape sh;
   Buffers b;
-  Carver dry;
-  const size_t need = carve(dry, sh, b, ctx->sm_count, ctx->cfg.precision);
-  rerank_status st = ensure_workspace(ctx, need);
-  if (st != RERANK_OK) return st;
-  Carver real;
-  real.base = ctx->ws;
-  carve(real, sh, b, ctx->sm_count, ctx->cfg.precision);
-  ctx->buf = b;
+  long long* st = nullptr;
+  const void* xq = nullptr;
+  const void* xg = nullptr;
+  int32_t* out_idx = nullptr;
+  float* out_dist = nullptr;
+};
 
-  auto& tm = ctx->timer;
-  tm.on = ctx->cfg.stage_timing != 0;
-  tm.stream = s;
-  tm.mark("begin");
+// Enqueue every stage of one instance on `s` (no host synchronisation).
+rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches) {
+  const Shape& sh = j.sh;
+  const Buffers& b = j.b;
+  long long* status = j.st;
+  auto mark = [&](const char* name) {
+    if (tm) tm->mark(name);
+  };
   int64_t nl = 1;
-  k_status_reset<<<1, 64, 0, s>>>(ctx->d_status);
+  k_status_reset<<<1, 64, 0, s>>>(status);
   RR_CUDA(cudaMemsetAsync(b.fb_count, 0, sizeof(int32_t), s));
   if (b.fb2_count) RR_CUDA(cudaMemsetAsync(b.fb2_count, 0, sizeof(int32_t), s));
-  const void* dq = xq;
-  const void* dg = xg;
+  const void* dq = j.xq;
+  const void* dg = j.xg;
   if (sh.host_in) {
     const size_t es = type_size(sh.dtype);
-    RR_CUDA(cudaMemcpyAsync(b.xq, xq, size_t(sh.nq) * sh.d * es, cudaMemcpyHostToDevice, s));
-    if (sh.ng) RR_CUDA(cudaMemcpyAsync(b.xg, xg, size_t(sh.ng) * sh.d * es, cudaMemcpyHostToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(b.xq, j.xq, size_t(sh.nq) * sh.d * es, cudaMemcpyHostToDevice, s));
+    if (sh.ng) RR_CUDA(cudaMemcpyAsync(b.xg, j.xg, size_t(sh.ng) * sh.d * es, cudaMemcpyHostToDevice, s));
     dq = b.xq;
     dg = b.xg;
-    tm.mark("h2d");
+    mark("h2d");
   }
   const int prec = ctx->cfg.precision;
-  nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xhi, b.xlo, b.xscale, b.err, b.emax, prec,
-                         ctx->d_status, s);
-  tm.mark("normalize");
+  nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xhi, b.xlo, b.xscale, b.err, b.emax, prec, status, s);
+  mark("normalize");
   ErrModel em;
   em.err = b.err;
   em.emax = b.emax;
@@ -235,7 +236,7 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
     em.eps = (sh.dp + 10) * kU32 * 1.01;
   } else {
     const int r = launch_sim_tc_topk(sh, b.xlow, prec == RERANK_PREC_FP8, b.xscale, b.row_floor, b.part_s, b.part_i,
-                                     ctx->d_status, ctx->sm_count, s);
+                                     status, ctx->sm_count, s);
     if (r < 0) return RERANK_ECUDA;
     nl += r;
     // Quantisation error enters per row; on top: the FP32 accumulation of dp/16
@@ -244,11 +245,11 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
     em.kind = 1;
     em.eps = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
   }
-  tm.mark("similarity_topk");
+  mark("similarity_topk");
   nl += launch_cluster_order(sh, b.part_s, b.part_i, b.nb4, b.label, b.ord_cnt, b.ord_start, b.ord_fill, b.order, s);
   nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, sh.P, em, b.order, nullptr, true, b.knn_idx,
-                      b.knn_score, b.fb_rows, b.fb_count, ctx->d_status, s);
-  tm.mark("refine");
+                      b.knn_score, b.fb_rows, b.fb_count, status, s);
+  mark("refine");
   const int32_t* exact_rows = b.fb_rows;
   const int32_t* exact_count = b.fb_count;
   if (prec != RERANK_PREC_FP32) {
@@ -257,81 +258,122 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
     // neighbour sits among many near-equal scores.
     nl += launch_gather_rows(b.fb_rows, b.fb_count, b.xhi, b.xlo, b.ahi, b.alo, sh.n, sh.dp, s);
     const int r = launch_sim_tc_split_topk(sh, sh.P3, b.ahi, b.alo, b.xhi, b.xlo, b.fb_rows, b.fb_count,
-                                           b.row_floor3, b.part3_s, b.part3_i, ctx->d_status, ctx->sm_count, s);
+                                           b.row_floor3, b.part3_s, b.part3_i, status, ctx->sm_count, s);
     if (r < 0) return RERANK_ECUDA;
     nl += r;
     ErrModel e3 = em;
     e3.kind = 2;
     e3.eps = (3 * (sh.dp / 16) + 32) * 2.0 * kU32 + 8.0 * kU32;
     nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3, e3, b.fb_rows, b.fb_count, false,
-                        b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, ctx->d_status, s);
+                        b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, status, s);
     exact_rows = b.fb2_rows;
     exact_count = b.fb2_count;
-    tm.mark("recheck");
+    mark("recheck");
   }
   float* fb_s = reinterpret_cast<float*>(b.scan_tmp);
   int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(ctx->sm_count) * fallback_warps() * sh.K);
   nl += launch_refine_fallback(sh, dq, dg, b.xhat, b.norm, b.knn_idx, b.knn_score, exact_rows, exact_count, fb_s, fb_i,
-                               ctx->d_status, ctx->sm_count, s);
-  tm.mark("exact_scan");
+                               status, ctx->sm_count, s);
+  mark("exact_scan");
   if (sh.knn_only) {
     const size_t bytes = size_t(sh.n) * sh.k1;
-    int32_t* oi = sh.host_out ? b.out_idx : out_idx;
-    float* os = sh.host_out ? b.out_dist : out_dist;
+    int32_t* oi = sh.host_out ? b.out_idx : j.out_idx;
+    float* os = sh.host_out ? b.out_dist : j.out_dist;
     RR_CUDA(cudaMemcpyAsync(oi, b.knn_idx, bytes * 4, cudaMemcpyDeviceToDevice, s));
     RR_CUDA(cudaMemcpyAsync(os, b.knn_score, bytes * 4, cudaMemcpyDeviceToDevice, s));
     if (sh.host_out) {
-      RR_CUDA(cudaMemcpyAsync(out_idx, b.out_idx, bytes * 4, cudaMemcpyDeviceToHost, s));
-      RR_CUDA(cudaMemcpyAsync(out_dist, b.out_dist, bytes * 4, cudaMemcpyDeviceToHost, s));
+      RR_CUDA(cudaMemcpyAsync(j.out_idx, b.out_idx, bytes * 4, cudaMemcpyDeviceToHost, s));
+      RR_CUDA(cudaMemcpyAsync(j.out_dist, b.out_dist, bytes * 4, cudaMemcpyDeviceToHost, s));
     }
   } else {
-    nl += launch_graph(sh, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, ctx->d_status, s);
-    tm.mark("graph");
+    nl += launch_graph(sh, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, status, s);
+    mark("graph");
     RR_CUDA(cudaMemsetAsync(b.hash_keys_vals, 0,
                             sizeof(float) * size_t(ctx->sm_count) * (size_t(sh.n) + size_t((sh.n + 31) / 32)), s));
     int src = 2;
     for (int l = 0; l < sh.layers; ++l) {
       const int dst = l & 1;
-      nl += launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, ctx->d_status, ctx->sm_count, ctx->tune, s);
+      nl += launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, ctx->sm_count, ctx->tune, s);
       src = dst;
     }
-    tm.mark("propagate");
-    nl += launch_row_norms(sh, b, src, ctx->d_status, s);
-    int32_t* oi = sh.host_out ? b.out_idx : out_idx;
-    float* od = sh.host_out ? b.out_dist : out_dist;
-    nl += launch_rank(sh, b, src, oi, od, ctx->d_status, ctx->sm_count, ctx->tune, s);
-    tm.mark("rank");
+    mark("propagate");
+    nl += launch_row_norms(sh, b, src, status, s);
+    int32_t* oi = sh.host_out ? b.out_idx : j.out_idx;
+    float* od = sh.host_out ? b.out_dist : j.out_dist;
+    nl += launch_rank(sh, b, src, oi, od, status, ctx->sm_count, ctx->tune, s);
+    mark("rank");
     if (sh.host_out) {
       const size_t cnt = size_t(sh.nq) * sh.topk;
-      RR_CUDA(cudaMemcpyAsync(out_idx, b.out_idx, cnt * 4, cudaMemcpyDeviceToHost, s));
-      RR_CUDA(cudaMemcpyAsync(out_dist, b.out_dist, cnt * 4, cudaMemcpyDeviceToHost, s));
-      tm.mark("d2h");
+      RR_CUDA(cudaMemcpyAsync(j.out_idx, b.out_idx, cnt * 4, cudaMemcpyDeviceToHost, s));
+      RR_CUDA(cudaMemcpyAsync(j.out_dist, b.out_dist, cnt * 4, cudaMemcpyDeviceToHost, s));
+      mark("d2h");
     }
   }
-  ctx->launches = nl;
-  RR_CUDA(cudaGetLastError());
-  st = collect(ctx, s);
-  if (tm.on) finish_timing(ctx);
-  if (st != RERANK_OK) return st;
-  const long long* h = ctx->h_status;
-  ctx->info.fp64_rescored = h[kStFp64];
-  ctx->info.fallback_rows = h[kStFallback];
-  ctx->info.exact_scan_rows = ctx->cfg.precision == RERANK_PREC_FP32 ? h[kStFallback] : h[kStFallback2];
-  ctx->info.error_bits = int32_t(h[kStErr]);
-  ctx->info.bad_row = h[kStBadRow] == LLONG_MAX ? -1 : int32_t(h[kStBadRow]);
+  *launches += nl;
+  return RERANK_OK;
+}
+
+// Map one instance's device status block to a return code; fills the info counters.
+// On a layer-buffer overflow, *need receives the capacity the layer asked for.
+rerank_status map_status(const long long* h, int precision, rerank_info* info, int64_t* need) {
+  info->fp64_rescored = h[kStFp64];
+  info->fallback_rows = h[kStFallback];
+  info->exact_scan_rows = precision == RERANK_PREC_FP32 ? h[kStFallback] : h[kStFallback2];
+  info->error_bits = int32_t(h[kStErr]);
+  info->bad_row = h[kStBadRow] == LLONG_MAX ? -1 : int32_t(h[kStBadRow]);
   const int e = int(h[kStErr]);
+  *need = 0;
   if (e & (kErrNonFinite | kErrZeroNorm)) return RERANK_EINVAL;
   if (e & kErrOverflow) {
-    ctx->cap_h_hint = std::max<int64_t>(ctx->cap_h_hint, int64_t(h[kStNeed]) + int64_t(h[kStNeed]) / 4 + 1024);
-    return RERANK_ENOMEM;  // caller of run_once retries with the larger capacity
+    *need = int64_t(h[kStNeed]);
+    return RERANK_ENOMEM;
   }
   if (e & kErrTimeout) return RERANK_ETIMEOUT;
   if (e & (kErrCertify | kErrInternal)) return RERANK_EINTERNAL;
   return RERANK_OK;
 }
 
-rerank_status plan(rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, int k1, int k2, int layers,
-                   int64_t topk, bool knn_only, bool host_in, bool host_out) {
+// One attempt of the pipeline.  Returns OK, or the mapped device error.
+rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t* out_idx, float* out_dist,
+                       cudaStream_t s) {
+  JobRun j;
+  j.sh = ctx->shape;
+  Carver dry;
+  const size_t need = carve(dry, j.sh, j.b, ctx->sm_count, ctx->cfg.precision);
+  rerank_status st = ensure_workspace(ctx, need);
+  if (st != RERANK_OK) return st;
+  Carver real;
+  real.base = ctx->ws;
+  carve(real, j.sh, j.b, ctx->sm_count, ctx->cfg.precision);
+  ctx->buf = j.b;
+  j.st = ctx->d_status;
+  j.xq = xq;
+  j.xg = xg;
+  j.out_idx = out_idx;
+  j.out_dist = out_dist;
+
+  auto& tm = ctx->timer;
+  tm.on = ctx->cfg.stage_timing != 0;
+  tm.stream = s;
+  tm.mark("begin");
+  int64_t nl = 0;
+  st = enqueue_job(ctx, j, s, &tm, &nl);
+  if (st != RERANK_OK) return st;
+  ctx->launches = nl;
+  RR_CUDA(cudaGetLastError());
+  st = collect(ctx, s);
+  if (tm.on) finish_timing(ctx);
+  if (st != RERANK_OK) return st;
+  int64_t want = 0;
+  st = map_status(ctx->h_status, ctx->cfg.precision, &ctx->info, &want);
+  // The caller of run_once retries an overflow with the larger capacity.
+  if (st == RERANK_ENOMEM) ctx->cap_h_hint = std::max<int64_t>(ctx->cap_h_hint, want + want / 4 + 1024);
+  return st;
+}
+
+// Shape of one instance.  cap_hint: a layer capacity learned from an earlier overflow.
+rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, int k1, int k2, int layers,
+                         int64_t topk, bool knn_only, bool host_in, bool host_out, int64_t cap_hint, Shape* out) {
   Shape sh;
   sh.nq = nq;
   sh.ng = ng;
@@ -362,11 +404,17 @@ rerank_status plan(rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, in
   // n^2 bounds it exactly for small graphs; otherwise a generous guess, grown on overflow.
   int64_t guess = std::max<int64_t>(2 * sh.n * k1, std::min<int64_t>(sh.n * sh.n, sh.n * int64_t(k2 + 1) * 160));
   if (ctx->test_cap_h > 0) guess = ctx->test_cap_h;
-  sh.cap_h = std::max<int64_t>(guess, ctx->cap_h_hint);
+  sh.cap_h = std::max<int64_t>(guess, cap_hint);
   sh.rank_ctas = ctx->sm_count;
   if (sh.n * int64_t(k1) >= (int64_t(1) << 31) || sh.n >= (int64_t(1) << 31) - 1) return RERANK_EUNSUPPORTED;
-  ctx->shape = sh;
+  *out = sh;
   return RERANK_OK;
+}
+
+rerank_status plan(rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, int k1, int k2, int layers,
+                   int64_t topk, bool knn_only, bool host_in, bool host_out) {
+  return plan_shape(ctx, nq, ng, d, dtype, k1, k2, layers, topk, knn_only, host_in, host_out, ctx->cap_h_hint,
+                    &ctx->shape);
 }
 
 rerank_status run_with_retry(rerank_ctx* ctx, const void* xq, const void* xg, int32_t* oi, float* od,
@@ -382,6 +430,137 @@ rerank_status run_with_retry(rerank_ctx* ctx, const void* xq, const void* xg, in
   ctx->info.n_vertices = ctx->shape.n;
   ctx->info.candidates_per_row = ctx->shape.K;
   return st;
+}
+
+constexpr int kBatchStreams = 8;
+
+rerank_status ensure_streams(rerank_ctx* ctx) {
+  if (!ctx->streams.empty()) return RERANK_OK;
+  for (int i = 0; i < kBatchStreams; ++i) {
+    cudaStream_t st = nullptr;
+    RR_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    ctx->streams.push_back(st);
+  }
+  for (int i = 0; i <= kBatchStreams; ++i) {
+    cudaEvent_t e = nullptr;
+    RR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->events.push_back(e);
+  }
+  return RERANK_OK;
+}
+
+rerank_status ensure_host_status(rerank_ctx* ctx, size_t count) {
+  if (count <= ctx->h_batch_count) return RERANK_OK;
+  if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
+  ctx->h_batch = nullptr;
+  ctx->h_batch_count = 0;
+  RR_CUDA(cudaMallocHost(&ctx->h_batch, count * sizeof(long long)));
+  ctx->h_batch_count = count;
+  return RERANK_OK;
+}
+
+// Rough device cost of an instance, used to spread instances over the streams.
+double job_cost(const Shape& sh) {
+  return double(sh.np) * double(sh.np) * double(sh.dp) + 4.0e4 * double(sh.n) * double(sh.k1);
+}
+
+rerank_status run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, cudaStream_t s) {
+  std::vector<JobRun> runs(static_cast<size_t>(njobs));
+  size_t total = 0;
+  const size_t st_bytes = sizeof(long long) * kStCount;
+  std::vector<size_t> off(static_cast<size_t>(njobs));
+  for (int i = 0; i < njobs; ++i) {
+    const rerank_job& jb = jobs[i];
+    const bool host_in = is_host_ptr(jb.xq) || is_host_ptr(jb.xg);
+    const bool host_out = is_host_ptr(jb.out_idx) || is_host_ptr(jb.out_dist);
+    const int64_t topk = jb.topk_out ? jb.topk_out : jb.ng;
+    rerank_status st = plan_shape(ctx, jb.nq, jb.ng, jb.d, jb.dtype, jb.k1, jb.k2, jb.layers, topk, false, host_in,
+                                  host_out, 0, &runs[size_t(i)].sh);
+    if (st != RERANK_OK) return st;
+    Carver dry;
+    const size_t need = carve(dry, runs[size_t(i)].sh, runs[size_t(i)].b, ctx->sm_count, ctx->cfg.precision);
+    total = (total + 255) & ~size_t(255);
+    off[size_t(i)] = total;
+    total += ((st_bytes + 255) & ~size_t(255)) + need;
+  }
+  rerank_status st = ensure_workspace(ctx, total);
+  if (st != RERANK_OK) return st;
+  st = ensure_streams(ctx);
+  if (st != RERANK_OK) return st;
+  st = ensure_host_status(ctx, size_t(njobs) * kStCount);
+  if (st != RERANK_OK) return st;
+  for (int i = 0; i < njobs; ++i) {
+    JobRun& j = runs[size_t(i)];
+    j.st = reinterpret_cast<long long*>(ctx->ws + off[size_t(i)]);
+    Carver real;
+    real.base = ctx->ws + off[size_t(i)] + ((st_bytes + 255) & ~size_t(255));
+    carve(real, j.sh, j.b, ctx->sm_count, ctx->cfg.precision);
+    j.xq = jobs[i].xq;
+    j.xg = jobs[i].xg;
+    j.out_idx = jobs[i].out_idx;
+    j.out_dist = jobs[i].out_dist;
+  }
+  // Largest instances first, each onto the least loaded stream.
+  std::vector<int> idx(static_cast<size_t>(njobs));
+  for (int i = 0; i < njobs; ++i) idx[size_t(i)] = i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) {
+    const double ca = job_cost(runs[size_t(a)].sh), cb = job_cost(runs[size_t(b)].sh);
+    return ca != cb ? ca > cb : a < b;
+  });
+  const int ns = std::min<int>(kBatchStreams, njobs);
+  std::vector<double> load(static_cast<size_t>(ns), 0.0);
+  RR_CUDA(cudaEventRecord(ctx->events[0], s));
+  for (int k = 0; k < ns; ++k) RR_CUDA(cudaStreamWaitEvent(ctx->streams[size_t(k)], ctx->events[0], 0));
+  int64_t nl = 0;
+  for (int i : idx) {
+    int k = 0;
+    for (int t = 1; t < ns; ++t)
+      if (load[size_t(t)] < load[size_t(k)]) k = t;
+    load[size_t(k)] += job_cost(runs[size_t(i)].sh);
+    st = enqueue_job(ctx, runs[size_t(i)], ctx->streams[size_t(k)], nullptr, &nl);
+    if (st != RERANK_OK) break;
+  }
+  for (int k = 0; k < ns; ++k) {
+    RR_CUDA(cudaEventRecord(ctx->events[size_t(1 + k)], ctx->streams[size_t(k)]));
+    RR_CUDA(cudaStreamWaitEvent(s, ctx->events[size_t(1 + k)], 0));
+  }
+  if (st != RERANK_OK) return st;
+  for (int i = 0; i < njobs; ++i)
+    RR_CUDA(cudaMemcpyAsync(ctx->h_batch + size_t(i) * kStCount, runs[size_t(i)].st, st_bytes,
+                            cudaMemcpyDeviceToHost, s));
+  RR_CUDA(cudaStreamSynchronize(s));
+  RR_CUDA(cudaGetLastError());
+  ctx->launches = nl;
+  rerank_status first = RERANK_OK;
+  rerank_info agg{};
+  for (int i = 0; i < njobs; ++i) {
+    rerank_info inf{};
+    int64_t want = 0;
+    rerank_status js = map_status(ctx->h_batch + size_t(i) * kStCount, ctx->cfg.precision, &inf, &want);
+    if (js == RERANK_ENOMEM) {
+      // Overflowed propagation buffers: rerun this instance alone with the capacity it asked for.
+      ctx->cap_h_hint = std::max<int64_t>(ctx->cap_h_hint, want + want / 4 + 1024);
+      const rerank_job& jb = jobs[i];
+      js = plan(ctx, jb.nq, jb.ng, jb.d, jb.dtype, jb.k1, jb.k2, jb.layers, runs[size_t(i)].sh.topk, false,
+                runs[size_t(i)].sh.host_in, runs[size_t(i)].sh.host_out);
+      if (js == RERANK_OK) js = run_with_retry(ctx, jb.xq, jb.xg, jb.out_idx, jb.out_dist, s);
+      nl += ctx->launches;
+      inf = ctx->info;
+    }
+    jobs[i].status = js;
+    if (js != RERANK_OK && first == RERANK_OK) first = js;
+    agg.n_vertices += runs[size_t(i)].sh.n;
+    agg.fp64_rescored += inf.fp64_rescored;
+    agg.fallback_rows += inf.fallback_rows;
+    agg.exact_scan_rows += inf.exact_scan_rows;
+    agg.error_bits |= inf.error_bits;
+  }
+  agg.bad_row = -1;
+  agg.workspace_bytes = int64_t(ctx->ws_bytes);
+  agg.kernel_launches = nl;
+  ctx->info = agg;
+  ctx->launches = nl;
+  return first;
 }
 
 bool valid_enum(const rerank_config* c) {
@@ -474,6 +653,9 @@ rerank_status rerank_destroy(rerank_ctx* ctx) {
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   for (auto e : ctx->timer.ev) cudaEventDestroy(e);
+  for (auto st : ctx->streams) cudaStreamDestroy(st);
+  for (auto e : ctx->events) cudaEventDestroy(e);
+  if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
   delete ctx;
   return RERANK_OK;
 }
@@ -492,6 +674,22 @@ rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void
   st = plan(ctx, nq, ng, d, dtype, k1, k2, layers, topk, false, host_in, host_out);
   if (st != RERANK_OK) return st;
   return run_with_retry(ctx, xq, xg, out_idx, out_dist, static_cast<cudaStream_t>(stream));
+}
+
+rerank_status rerank_run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, void* stream) {
+  if (!ctx || !jobs || njobs < 1) return RERANK_EINVAL;
+  if (ctx->cfg.aggregator == RERANK_AGG_MAX || ctx->cfg.feature_mode == RERANK_FEAT_X) return RERANK_EUNSUPPORTED;
+  rerank_status bad = RERANK_OK;
+  for (int i = 0; i < njobs; ++i) {
+    rerank_job& j = jobs[i];
+    j.status = (!j.xq || !j.xg || !j.out_idx || !j.out_dist)
+                   ? RERANK_EINVAL
+                   : rerank_check_args(j.nq, j.ng, j.d, j.dtype, j.k1, j.k2, j.layers, j.topk_out);
+    if (j.status != RERANK_OK && bad == RERANK_OK) bad = j.status;
+  }
+  if (bad != RERANK_OK) return bad;
+  RR_CUDA(cudaSetDevice(ctx->device));
+  return run_batch(ctx, jobs, njobs, static_cast<cudaStream_t>(stream));
 }
 
 rerank_status rerank_knn(rerank_ctx* ctx, const void* x, int64_t n, int d, int dtype, int k, int32_t* out_idx,

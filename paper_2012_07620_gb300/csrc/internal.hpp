@@ -158,6 +158,12 @@ struct rerank_ctx {
   int64_t launches = 0;
   rr::Buffers buf{};
   rr::Shape shape{};
+  // batched calls: internal streams forked from the caller's, fork/join events,
+  // and a pinned copy of every instance's status block
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;   // [0] fork, [1 + i] join of streams[i]
+  long long* h_batch = nullptr;
+  size_t h_batch_count = 0;
 };
 
 namespace rr {

@@ -43,6 +43,13 @@ class RerankInfo(ctypes.Structure):
                 ("error_bits", ctypes.c_int32), ("bad_row", ctypes.c_int32)]
 
 
+class RerankJob(ctypes.Structure):
+    _fields_ = [("xq", ctypes.c_void_p), ("nq", ctypes.c_int64), ("xg", ctypes.c_void_p), ("ng", ctypes.c_int64),
+                ("d", ctypes.c_int), ("dtype", ctypes.c_int), ("k1", ctypes.c_int), ("k2", ctypes.c_int),
+                ("layers", ctypes.c_int), ("topk_out", ctypes.c_int64), ("out_idx", ctypes.c_void_p),
+                ("out_dist", ctypes.c_void_p), ("status", ctypes.c_int)]
+
+
 class RerankError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -61,6 +68,7 @@ _SIGS = {
     "rerank_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "rerank_run_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RerankJob), ctypes.c_int, ctypes.c_void_p]),
     "rerank_knn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rerank_last_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RerankInfo)]),
@@ -199,6 +207,29 @@ class Reranker:
                                   _ptr(out_idx), _ptr(out_dist), _stream_handle(stream))
         _check(st, "rerank_run")
         return out_idx, out_dist
+
+    def run_batch(self, jobs, stream=None):
+        """Many independent instances in one call (``rerank_run_batch``).
+
+        ``jobs``: list of dicts with keys xq, xg, k1, k2, layers and optionally
+        topk_out, out_idx, out_dist.  Returns a list of (out_idx, out_dist)."""
+        arr = (RerankJob * len(jobs))()
+        outs = []
+        for i, j in enumerate(jobs):
+            xq, xg = j["xq"], j["xg"]
+            nq, d = xq.shape
+            ng = xg.shape[0]
+            topk = j.get("topk_out", 0)
+            oi, od = j.get("out_idx"), j.get("out_dist")
+            if oi is None:
+                oi, od = self._alloc_out(xq, (nq, topk if topk else ng))
+            outs.append((oi, od))
+            arr[i] = RerankJob(_ptr(xq), nq, _ptr(xg), ng, d, _dtype_code(xq), j["k1"], j["k2"], j["layers"], topk,
+                               _ptr(oi), _ptr(od), 0)
+        st = self._lib.rerank_run_batch(self._h, arr, len(jobs), _stream_handle(stream))
+        self.batch_status = [arr[i].status for i in range(len(jobs))]
+        _check(st, "rerank_run_batch")
+        return outs
 
     def knn(self, x, k: int, out_idx=None, out_score=None, stream=None):
         """Exact top-k neighbour lists (Eq. 7-8) of every row of x; returns (idx, score)."""
