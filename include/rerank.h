@@ -139,6 +139,87 @@ typedef struct {
  * return EINVAL before anything runs. */
 rerank_status rerank_run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, void* stream);
 
+/* ---- Serving: a resident gallery and a request loop ----
+ *
+ * Each request brings nq new query vectors and is answered exactly as
+ * Algorithm 1 on X_u = (its queries) u (the resident gallery), queries first
+ * (Sec. 3.3): no other request's queries take part.  What depends on the
+ * gallery alone is computed once at load and kept on the device: the unit
+ * rows and their BF16/FP8 copies, every gallery row's candidate list and its
+ * exact top-k1 list.  Per request the library scores the queries against
+ * X_u and the gallery against the queries (tensor cores), re-derives the
+ * exact top-k1 list of every gallery row that a query can enter (the others
+ * keep their resident lists, which stay exact), and runs the graph,
+ * propagation and ranking stages on X_u.
+ *
+ * Requests are admitted into slots: each slot owns a stream and the device
+ * buffers of one request of up to max_query queries.  The slot count is set
+ * at load by the context's hbm_budget (every slot must fit, beside the
+ * resident gallery) and by `slots`.  A request submitted while every slot is
+ * busy waits in a host queue and starts as soon as a slot frees, while the
+ * other slots' work is still on the GPU; slots run concurrently.  Results
+ * depend only on the request and the gallery, never on which other requests
+ * share the GPU.  Tensor-core precision only (cfg.precision BF16 or FP8).
+ * One thread waits on a ticket at a time.  The caller keeps a request's buffers
+ * alive and unchanged until rerank_wait has returned its final status. */
+typedef struct {
+  int64_t max_query; /* largest nq of a request, 1 .. 1024 */
+  int slots;         /* concurrent requests on the GPU; 0 = as many as hbm_budget allows, at most 8 */
+  int k1, k2, layers;
+} rerank_serve_config;
+
+typedef struct {
+  const void* xq;   /* nq x d query features (host or device memory), the gallery's dtype */
+  int64_t nq;       /* 1 .. max_query */
+  int64_t topk_out; /* length of each output list; 0 = the whole gallery */
+  int32_t* out_idx; /* nq x topk_out (host or device), gallery indices best first */
+  float* out_dist;  /* nq x topk_out, 1 - cos(h_q, h_g) */
+  void* stream;     /* cudaStream_t on which the caller produced xq (NULL = legacy default stream):
+                       the request reads xq only after the work queued there before the submit */
+} rerank_request;
+
+typedef struct {
+  rerank_status status; /* the request's result code */
+  double queue_ms;      /* submit -> its work enqueued on a slot */
+  double total_ms;      /* submit -> results in the output buffers (host clock) */
+  int slot;             /* slot that ran it */
+} rerank_ticket_info;
+
+/* Load the resident gallery (ng x d, host or device memory; copied) and start
+ * the request loop.  Synchronous.  Errors: EINVAL (sizes, k2 > k1, ng <
+ * k1 + rescore_m, max_query < 1), EUNSUPPORTED (FP32 precision, or a gallery
+ * already loaded), EBUDGET (the resident data and one slot exceed hbm_budget),
+ * ENOMEM, ECUDA, and any status of the gallery's own neighbour lists. */
+rerank_status rerank_gallery_load(rerank_ctx* ctx, const void* xg, int64_t ng, int d, int dtype,
+                                  const rerank_serve_config* sc);
+
+/* Queue one request; *ticket identifies it.  The caller keeps the request's
+ * buffers alive and untouched until rerank_wait reports it finished.
+ * Errors: EINVAL (null pointers, nq outside 1 .. max_query, topk_out > ng),
+ * EUNSUPPORTED (no gallery loaded). */
+rerank_status rerank_submit(rerank_ctx* ctx, const rerank_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_ms (< 0: without limit) for a request.  Returns EAGAIN
+ * if it is still running (the ticket stays valid), else the request's status;
+ * *info (may be NULL) receives its timings.  A finished ticket is released by
+ * this call.  EINVAL for an unknown ticket. */
+rerank_status rerank_wait(rerank_ctx* ctx, uint64_t ticket, int timeout_ms, rerank_ticket_info* info);
+
+/* Counters of the request loop. */
+typedef struct {
+  int slots;                 /* slots admitted by the budget */
+  int max_in_flight;         /* most requests on the GPU at once so far */
+  int64_t completed;
+  int64_t touched_rows;      /* gallery rows re-derived, summed over requests */
+  int64_t resident_bytes;    /* gallery data kept on the device */
+  int64_t slot_bytes;        /* device memory of one slot */
+} rerank_serve_info;
+rerank_status rerank_serve_info_get(const rerank_ctx* ctx, rerank_serve_info* info);
+
+/* Finish every queued and running request, stop the loop and free the
+ * gallery and the slots.  Also done by rerank_destroy. */
+rerank_status rerank_gallery_unload(rerank_ctx* ctx);
+
 /* Steps 1-2 only: the exact top-k neighbour lists of every vertex of X (Eq. 7-8).
  *   x          n x d features (dtype)
  *   out_idx    n x k int32, sorted by (S desc, index asc); out_idx[i*k] == i

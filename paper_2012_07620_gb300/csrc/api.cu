@@ -36,11 +36,14 @@ int sim_fp32_kmax();
 int refine_kmax();
 int fallback_warps();
 
-namespace {
-
 __global__ void k_status_reset(long long* st) {
   const int t = threadIdx.x;
   if (t < kStCount) st[t] = (t == kStBadRow) ? LLONG_MAX : 0;
+}
+
+int launch_status_reset(long long* st, cudaStream_t s) {
+  k_status_reset<<<1, 64, 0, s>>>(st);
+  return 1;
 }
 
 bool is_host_ptr(const void* p) {
@@ -85,17 +88,22 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
     b.out_idx = c.take<int32_t>(size_t(sh.nq) * (sh.knn_only ? k1 : sh.topk));
     b.out_dist = c.take<float>(size_t(sh.nq) * (sh.knn_only ? k1 : sh.topk));
   }
-  b.xhat = c.take<float>(size_t(np) * sh.dp);
-  b.xlow = precision == RERANK_PREC_FP32
-               ? nullptr
-               : c.take<char>(size_t(np) * sh.dp * (precision == RERANK_PREC_FP8 ? 1 : 2));
-  b.xscale = c.take<float>(size_t(np));
-  b.err = c.take<float>(3 * size_t(np));
-  b.emax = c.take<float>(4);
+  if (!sh.ext_feat) {
+    b.xhat = c.take<float>(size_t(np) * sh.dp);
+    b.xlow = precision == RERANK_PREC_FP32
+                 ? nullptr
+                 : c.take<char>(size_t(np) * sh.dp * (precision == RERANK_PREC_FP8 ? 1 : 2));
+    b.xscale = c.take<float>(size_t(np));
+    b.err = c.take<float>(3 * size_t(np));
+    b.emax = c.take<float>(4);
+    b.norm = c.take<double>(size_t(np));
+  }
   if (precision != RERANK_PREC_FP32) {
-    b.xhi = precision == RERANK_PREC_BF16 ? static_cast<__nv_bfloat16*>(b.xlow)
-                                          : c.take<__nv_bfloat16>(size_t(np) * sh.dp);
-    b.xlo = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
+    if (!sh.ext_feat) {
+      b.xhi = precision == RERANK_PREC_BF16 ? static_cast<__nv_bfloat16*>(b.xlow)
+                                            : c.take<__nv_bfloat16>(size_t(np) * sh.dp);
+      b.xlo = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
+    }
     b.ahi = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
     b.alo = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
     b.part3_s = c.take<float>(size_t(n) * sh.P3 * sh.K);
@@ -111,7 +119,6 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
   b.ord_cnt = c.take<int32_t>(size_t(n) + 1);
   b.ord_start = c.take<int32_t>(size_t(n) + 1);
   b.ord_fill = c.take<int32_t>(size_t(n));
-  b.norm = c.take<double>(size_t(np));
   b.part_s = c.take<float>(size_t(n) * sh.P * sh.K);
   b.part_i = c.take<int32_t>(size_t(n) * sh.P * sh.K);
   b.knn_idx = c.take<int32_t>(size_t(n) * k1);
@@ -188,17 +195,6 @@ void finish_timing(rerank_ctx* ctx) {
   tm.ev.clear();
   tm.names.clear();
 }
-
-// One pipeline instance: its shape, its buffers and its device status block.
-struct JobRun {
-  Shape sh;
-  Buffers b;
-  long long* st = nullptr;
-  const void* xq = nullptr;
-  const void* xg = nullptr;
-  int32_t* out_idx = nullptr;
-  float* out_dist = nullptr;
-};
 
 // Enqueue every stage of one instance on `s` (no host synchronisation).
 rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches) {
@@ -568,7 +564,6 @@ bool valid_enum(const rerank_config* c) {
          c->feature_mode >= 0 && c->feature_mode <= 2 && c->rescore_m >= 0 && c->rescore_m <= 256;
 }
 
-}  // namespace
 }  // namespace rr
 
 using namespace rr;
@@ -648,6 +643,7 @@ rerank_status rerank_create(rerank_ctx** out, const rerank_config* cfg) {
 
 rerank_status rerank_destroy(rerank_ctx* ctx) {
   if (!ctx) return RERANK_OK;
+  serve_stop(ctx);
   cudaSetDevice(ctx->device);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_status) cudaFree(ctx->d_status);

@@ -29,6 +29,7 @@ enum : int {
   kStFallback = 3,     // rows whose first candidate list was not certified
   kStFallback2 = 5,    // rows that needed the exact full-row scan
   kStNeed = 4,         // capacity needed by the stage that overflowed (elements)
+  kStTouched = 6,      // serving: gallery rows whose neighbour list a request re-derived
   kStNnz0 = 8,         // nnz of h^(l) at kStNnz0 + l, l <= 8
   kStCount = 32
 };

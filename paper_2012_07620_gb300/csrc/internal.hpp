@@ -120,12 +120,15 @@ struct Shape {
   int64_t topk = 0;
   bool host_in = false, host_out = false;
   bool knn_only = false;
+  bool ext_feat = false;   // the unit rows and their copies live outside the workspace (serving)
   int64_t cap_h = 0;       // elements per padded-CSR layer buffer
   int64_t cap_csc = 0;
   int hash_slots = 0;      // slots of each global hash table (big-row path)
   int rank_ctas = 0;
   int64_t rank_scratch_per_cta = 0;
 };
+
+struct ServeHandle;  // the request loop of a loaded gallery (serve.cu)
 
 struct StageTimer {
   bool on = false;
@@ -164,6 +167,7 @@ struct rerank_ctx {
   std::vector<cudaEvent_t> events;   // [0] fork, [1 + i] join of streams[i]
   long long* h_batch = nullptr;
   size_t h_batch_count = 0;
+  rr::ServeHandle* serve = nullptr;
 };
 
 namespace rr {
@@ -181,6 +185,15 @@ int launch_sim_fp32_topk(const Shape& sh, const float* xhat, int* row_floor, flo
                          int sm_count, cudaStream_t s);
 int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float* inv_scale, int* row_floor,
                        float* part_s, int32_t* part_i, long long* status, int sm_count, cudaStream_t s);
+// Rectangular block: rows of `a` (a_rows of them, vertices row0 ..) against the
+// columns of `b` (b_cols, vertices col0 ..); per row P lists of its best K
+// columns (vertex indices) in part_s/part_i [a_rows][P][K].  Rows and columns
+// beyond the counts are never listed; `a` and `b` must hold at least
+// max(count, 256) rows (the tensor maps span whole tiles).
+int launch_sim_tc_rect_topk(const Shape& sh, const void* a, int64_t a_rows, int64_t row0, const void* b,
+                            int64_t b_cols, int64_t col0, int chunks, bool fp8, const float* inv_scale,
+                            int* row_floor, float* part_s, int32_t* part_i, long long* status, int sm_count,
+                            cudaStream_t s);
 // hi/lo split: S' = hi_i.hi_j + lo_i.hi_j + hi_i.lo_j for the rows rows[0 .. *count)
 // (their hi/lo copies gathered in ahi/alo) against every column; lists indexed by
 // position in `rows`, P3 chunks.
@@ -203,7 +216,7 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
                    const double* norm, const float* part_s, const int32_t* part_i, int P, const ErrModel& em,
                    const int32_t* rows, const int32_t* count, bool part_by_row,
                    int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
-                   long long* status, cudaStream_t s);
+                   long long* status, cudaStream_t s, int64_t grid_rows = -1);  // grid_rows: bound on the row count
 size_t tc_smem_bytes();
 int tc_kmax();
 int launch_refine_fallback(const Shape& sh, const void* xq, const void* xg, const float* xhat,
@@ -224,6 +237,30 @@ int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, fl
                  long long* status, int sm_count, const Tuning& t, cudaStream_t s);
 
 size_t rank_smem_bytes(int64_t ng, int threads);
+
+// ---- pipeline pieces shared by the single, batched and serving entry points ----
+// One pipeline instance: its shape, its buffers and its device status block.
+struct JobRun {
+  Shape sh;
+  Buffers b;
+  long long* st = nullptr;
+  const void* xq = nullptr;
+  const void* xg = nullptr;
+  int32_t* out_idx = nullptr;
+  float* out_dist = nullptr;
+};
+bool is_host_ptr(const void* p);
+size_t type_size(int dtype);
+int choose_chunks(int64_t row_blocks, int64_t col_tiles, int sm_count, int forced);
+size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision);
+rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, int k1, int k2,
+                         int layers, int64_t topk, bool knn_only, bool host_in, bool host_out, int64_t cap_hint,
+                         Shape* out);
+rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches);
+rerank_status map_status(const long long* h, int precision, rerank_info* info, int64_t* need);
+int launch_status_reset(long long* st, cudaStream_t s);
+// Stop the request loop of a loaded gallery and free it (no-op without one).
+rerank_status serve_stop(rerank_ctx* ctx);
 int propagate_warp_slots();
 
 }  // namespace rr

@@ -64,7 +64,10 @@ struct alignas(1024) TcSmem {
 };
 
 struct TcArgs {
-  int64_t n;                // columns (and rows, outside split mode)
+  int64_t n;                // columns of B (valid column indices 0 .. n-1)
+  int64_t a_rows;           // outside split mode: valid rows of A
+  int64_t row0;             // outside split mode: vertex index of A row 0
+  int64_t col0;             // vertex index of B column 0
   int row_blocks;           // outside split mode
   int col_tiles, chunks, kblocks, K;
   const float* inv_scale;   // FP8 only: 1 / s_i per row
@@ -98,7 +101,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort = &sm.abort;
   constexpr int SEGS = MODE == MODE_SPLIT ? 3 : 1;
-  const int64_t nrows = MODE == MODE_SPLIT ? int64_t(*A.count) : A.n;
+  const int64_t nrows = MODE == MODE_SPLIT ? int64_t(*A.count) : A.a_rows;
   const int row_blocks = MODE == MODE_SPLIT ? int((nrows + TBM - 1) / TBM) : A.row_blocks;
   const int items = row_blocks * A.chunks;
   const int kb_total = A.kblocks * SEGS;
@@ -237,7 +240,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       item_range(A, row_blocks, item, rb, chunk, t0, t1);
       const int64_t arow = int64_t(rb) * TBM + r;   // row of the A operand
       const bool live = arow < nrows;
-      const int64_t grow = MODE == MODE_SPLIT ? (live ? int64_t(A.rows[arow]) : -1) : arow;  // vertex
+      const int64_t grow = MODE == MODE_SPLIT ? (live ? int64_t(A.rows[arow]) : -1) : A.row0 + arow;  // vertex
       // This row's best KL columns so far in registers, as packed keys
       // (score_key << 32 | (INT_MAX - column)): a larger key is a better
       // column (score desc, column asc).  Sorted descending; empty slots hold
@@ -263,17 +266,19 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
           // warp-convergent drain: every round each lane inserts at most one
           // admitted column with a branch-free pass over its list, so the
           // warp pays per round, not per column.
-          const int64_t cbase = int64_t(ct) * TBN + cb * 32;
+          const int64_t lbase = int64_t(ct) * TBN + cb * 32;  // B column
+          const int64_t cbase = A.col0 + lbase;                // its vertex
           const long long thr = lk[KL - 1];
           uint32_t mask = 0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int64_t col = cbase + j;
+            const bool valid = lbase + j < A.n;
             float s = __uint_as_float(v[j]);
-            if (MODE == MODE_FP8) s = s * rinv * __ldg(A.inv_scale + (col < A.n ? col : 0));
+            if (MODE == MODE_FP8) s = s * rinv * __ldg(A.inv_scale + (valid ? col : 0));
             if (col == grow) s = 1.0f;
             sm.batch[j][r] = s;
-            const bool adm = live && col < A.n && s >= floor_s && pack_key(s, int(col)) > thr;
+            const bool adm = live && valid && s >= floor_s && pack_key(s, int(col)) > thr;
             mask |= adm ? (1u << j) : 0u;
           }
           int rounds = __popc(mask);
@@ -411,6 +416,7 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   cudaMemsetAsync(row_floor, kFloorResetByte, sizeof(int) * size_t(sh.n), s);
   TcArgs A{};
   A.n = sh.n;
+  A.a_rows = sh.n;
   A.row_blocks = int(sh.np / TBM);
   A.col_tiles = int(sh.np / TBN);
   A.chunks = sh.P;
@@ -427,6 +433,41 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
     launch_mode<MODE_FP8>(map, map, map, map, A, grid, s);
   else
     launch_mode<MODE_BF16>(map, map, map, map, A, grid, s);
+  return 1;
+}
+
+int launch_sim_tc_rect_topk(const Shape& sh, const void* a, int64_t a_rows, int64_t row0, const void* b,
+                            int64_t b_cols, int64_t col0, int chunks, bool fp8, const float* inv_scale,
+                            int* row_floor, float* part_s, int32_t* part_i, long long* status, int sm_count,
+                            cudaStream_t s) {
+  // The maps span at least one full tile (the caller's buffers hold that many rows).
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, a, a_rows > TBN ? a_rows : TBN, sh.dp, fp8) ||
+      !make_map(&mb, b, b_cols > TBN ? b_cols : TBN, sh.dp, fp8))
+    return -1;
+  cudaMemsetAsync(row_floor, kFloorResetByte, sizeof(int) * size_t(a_rows), s);
+  TcArgs A{};
+  A.n = b_cols;
+  A.a_rows = a_rows;
+  A.row0 = row0;
+  A.col0 = col0;
+  A.row_blocks = int((a_rows + TBM - 1) / TBM);
+  A.col_tiles = int((b_cols + TBN - 1) / TBN);
+  if (chunks < 1 || chunks > A.col_tiles) return -1;  // the caller reads exactly `chunks` lists per row
+  A.chunks = chunks;
+  A.kblocks = fp8 ? sh.dp / 128 : sh.dp / 64;
+  A.K = sh.K;
+  A.inv_scale = inv_scale;
+  A.row_floor = row_floor;
+  A.part_s = part_s;
+  A.part_i = part_i;
+  A.status = status;
+  const int items = A.row_blocks * A.chunks;
+  const int grid = items < sm_count ? items : sm_count;
+  if (fp8)
+    launch_mode<MODE_FP8>(ma, ma, mb, mb, A, grid, s);
+  else
+    launch_mode<MODE_BF16>(ma, ma, mb, mb, A, grid, s);
   return 1;
 }
 

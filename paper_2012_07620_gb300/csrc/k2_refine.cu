@@ -357,9 +357,10 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
                    const float* part_s, const int32_t* part_i, int P, const ErrModel& em, const int32_t* rows,
                    const int32_t* count, bool part_by_row, int32_t* knn_idx, float* knn_score,
                    int32_t* fb_rows, int32_t* fb_count,
-                   long long* status, cudaStream_t s) {
+                   long long* status, cudaStream_t s, int64_t grid_rows) {
   RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
-  const unsigned blocks = unsigned((sh.n + WPB - 1) / WPB);
+  const int64_t g = grid_rows > 0 && grid_rows < sh.n ? grid_rows : sh.n;
+  const unsigned blocks = unsigned((g + WPB - 1) / WPB);
   // First pass: uncertified rows go to the recheck; a recheck's failures go to the exact scan.
   const int stat = (rows && !part_by_row) ? kStFallback2 : kStFallback;
   k2_refine<<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em, rescore_eps(sh.dp), rows,

@@ -50,6 +50,27 @@ class RerankJob(ctypes.Structure):
                 ("out_dist", ctypes.c_void_p), ("status", ctypes.c_int)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("max_query", ctypes.c_int64), ("slots", ctypes.c_int), ("k1", ctypes.c_int), ("k2", ctypes.c_int),
+                ("layers", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("xq", ctypes.c_void_p), ("nq", ctypes.c_int64), ("topk_out", ctypes.c_int64),
+                ("out_idx", ctypes.c_void_p), ("out_dist", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+
+
+class TicketInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("queue_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("slot", ctypes.c_int)]
+
+
+class ServeInfo(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_in_flight", ctypes.c_int), ("completed", ctypes.c_int64),
+                ("touched_rows", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
+                ("slot_bytes", ctypes.c_int64)]
+
+
 class RerankError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -69,6 +90,12 @@ _SIGS = {
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rerank_run_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RerankJob), ctypes.c_int, ctypes.c_void_p]),
+    "rerank_gallery_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
+                                           ctypes.c_int, ctypes.POINTER(ServeConfig)]),
+    "rerank_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "rerank_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(TicketInfo)]),
+    "rerank_serve_info_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServeInfo)]),
+    "rerank_gallery_unload": (ctypes.c_int, [ctypes.c_void_p]),
     "rerank_knn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rerank_last_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RerankInfo)]),
@@ -174,6 +201,7 @@ class Reranker:
         self._h = h
         self._lib = lib
         self.device = device
+        self._live = {}
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -230,6 +258,49 @@ class Reranker:
         self.batch_status = [arr[i].status for i in range(len(jobs))]
         _check(st, "rerank_run_batch")
         return outs
+
+    # ---- serving ----
+    def load_gallery(self, xg, max_query: int, k1: int, k2: int, layers: int, slots: int = 0) -> None:
+        """Make ``xg`` the resident gallery and start the request loop (``rerank_gallery_load``)."""
+        ng, d = xg.shape
+        sc = ServeConfig(max_query, slots, k1, k2, layers)
+        _check(self._lib.rerank_gallery_load(self._h, _ptr(xg), ng, d, _dtype_code(xg), ctypes.byref(sc)),
+               "rerank_gallery_load")
+        self._gallery_rows = ng
+
+    def submit(self, xq, topk_out: int = 0, out_idx=None, out_dist=None, stream=None) -> tuple:
+        """Queue one request; returns (ticket, out_idx, out_dist).  The binding
+        keeps the three buffers alive until ``wait`` returns for the ticket; the
+        request reads ``xq`` after the work already queued on ``stream``
+        (default: the current torch stream)."""
+        nq = xq.shape[0]
+        t = topk_out if topk_out else self._gallery_rows
+        if out_idx is None:
+            out_idx, out_dist = self._alloc_out(xq, (nq, t))
+        rq = Request(_ptr(xq), nq, topk_out, _ptr(out_idx), _ptr(out_dist), _stream_handle(stream))
+        ticket = ctypes.c_uint64()
+        _check(self._lib.rerank_submit(self._h, ctypes.byref(rq), ctypes.byref(ticket)), "rerank_submit")
+        self._live[ticket.value] = (xq, out_idx, out_dist)
+        return ticket.value, out_idx, out_dist
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        """Wait for a request; returns its timings (raises on a failed request,
+        returns None while it is still running after ``timeout_ms``)."""
+        info = TicketInfo()
+        st = self._lib.rerank_wait(self._h, ticket, timeout_ms, ctypes.byref(info))
+        if st == 8:
+            return None
+        self._live.pop(ticket, None)
+        _check(st, "rerank_wait")
+        return {"queue_ms": info.queue_ms, "total_ms": info.total_ms, "slot": info.slot}
+
+    def serve_info(self) -> dict:
+        info = ServeInfo()
+        _check(self._lib.rerank_serve_info_get(self._h, ctypes.byref(info)), "rerank_serve_info_get")
+        return {f: getattr(info, f) for f, _ in ServeInfo._fields_}
+
+    def unload_gallery(self) -> None:
+        _check(self._lib.rerank_gallery_unload(self._h), "rerank_gallery_unload")
 
     def knn(self, x, k: int, out_idx=None, out_score=None, stream=None):
         """Exact top-k neighbour lists (Eq. 7-8) of every row of x; returns (idx, score)."""
