@@ -220,6 +220,36 @@ rerank_status rerank_serve_info_get(const rerank_ctx* ctx, rerank_serve_info* in
  * gallery and the slots.  Also done by rerank_destroy. */
 rerank_status rerank_gallery_unload(rerank_ctx* ctx);
 
+/* ---- Autotuner ----
+ * Launch shapes per (precision, d, bucket of N = nq + ng; buckets are half
+ * octaves, floor(2 log2 N)).  None of them changes a result, only the work
+ * decomposition (the paper fixes no schedule; these are GPU choices):
+ *   sim_chunks    column chunks of the similarity top-K kernel (0 = SM-count heuristic)
+ *   prop_warps    warps per CTA of the propagation kernel
+ *   refine_order  1 = refine rows cluster by cluster, 0 = in index order */
+typedef struct {
+  int sim_chunks;
+  int prop_warps;
+  int refine_order;
+  int n_bucket;
+  double ms; /* pipeline time measured with this choice */
+} rerank_tuning;
+
+/* Time the pipeline on the caller's instance under candidate launch shapes
+ * (coordinate descent, median of three runs per candidate), store the best
+ * for this (precision, d, N bucket) in the context, and, when
+ * cfg.autotune_path was set, rewrite that JSON file with the context's whole
+ * table.  Later calls of this context (and contexts created with the same
+ * path) use the entry for every instance in the bucket.  Synchronous; runs
+ * the instance about 60 times.  *out (may be NULL) receives the choice.
+ * Errors: as rerank_run; EINVAL if the table file cannot be written. */
+rerank_status rerank_autotune(rerank_ctx* ctx, const void* xq, int64_t nq, const void* xg, int64_t ng, int d,
+                              int dtype, int k1, int k2, int layers, rerank_tuning* out, void* stream);
+
+/* Host only: the entry of a tuning table file for (precision, n, d).
+ * EINVAL if the file is missing or unreadable, EAGAIN if it has no entry. */
+rerank_status rerank_tuning_lookup(const char* path, int precision, int64_t n, int d, rerank_tuning* out);
+
 /* Steps 1-2 only: the exact top-k neighbour lists of every vertex of X (Eq. 7-8).
  *   x          n x d features (dtype)
  *   out_idx    n x k int32, sorted by (S desc, index asc); out_idx[i*k] == i

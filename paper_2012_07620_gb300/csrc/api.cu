@@ -241,10 +241,17 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     em.kind = 1;
     em.eps = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
   }
+  RR_CUDA(cudaGetLastError());
   mark("similarity_topk");
-  nl += launch_cluster_order(sh, b.part_s, b.part_i, b.nb4, b.label, b.ord_cnt, b.ord_start, b.ord_fill, b.order, s);
-  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, sh.P, em, b.order, nullptr, true, b.knn_idx,
+  const int32_t* order = nullptr;
+  if (sh.tune.refine_order) {
+    nl += launch_cluster_order(sh, b.part_s, b.part_i, b.nb4, b.label, b.ord_cnt, b.ord_start, b.ord_fill, b.order,
+                               s);
+    order = b.order;
+  }
+  nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part_s, b.part_i, sh.P, em, order, nullptr, true, b.knn_idx,
                       b.knn_score, b.fb_rows, b.fb_count, status, s);
+  RR_CUDA(cudaGetLastError());
   mark("refine");
   const int32_t* exact_rows = b.fb_rows;
   const int32_t* exact_count = b.fb_count;
@@ -264,6 +271,7 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
                         b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, status, s);
     exact_rows = b.fb2_rows;
     exact_count = b.fb2_count;
+    RR_CUDA(cudaGetLastError());
     mark("recheck");
   }
   float* fb_s = reinterpret_cast<float*>(b.scan_tmp);
@@ -283,20 +291,23 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     }
   } else {
     nl += launch_graph(sh, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, status, s);
+    RR_CUDA(cudaGetLastError());
     mark("graph");
     RR_CUDA(cudaMemsetAsync(b.hash_keys_vals, 0,
                             sizeof(float) * size_t(ctx->sm_count) * (size_t(sh.n) + size_t((sh.n + 31) / 32)), s));
     int src = 2;
     for (int l = 0; l < sh.layers; ++l) {
       const int dst = l & 1;
-      nl += launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, ctx->sm_count, ctx->tune, s);
+      nl += launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, ctx->sm_count, sh.tune, s);
       src = dst;
     }
+    RR_CUDA(cudaGetLastError());
     mark("propagate");
     nl += launch_row_norms(sh, b, src, status, s);
     int32_t* oi = sh.host_out ? b.out_idx : j.out_idx;
     float* od = sh.host_out ? b.out_dist : j.out_dist;
-    nl += launch_rank(sh, b, src, oi, od, status, ctx->sm_count, ctx->tune, s);
+    nl += launch_rank(sh, b, src, oi, od, status, ctx->sm_count, sh.tune, s);
+    RR_CUDA(cudaGetLastError());
     mark("rank");
     if (sh.host_out) {
       const size_t cnt = size_t(sh.nq) * sh.topk;
@@ -393,7 +404,8 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
   int64_t K = std::min<int64_t>(int64_t(k1) + std::max(ctx->cfg.rescore_m, 0), sh.n);
   K = std::min<int64_t>(K, kmax);
   sh.K = int(K);
-  sh.P = choose_chunks(sh.np / 128, sh.np / (tc ? 256 : 128), ctx->sm_count, ctx->tune.sim_chunks);
+  sh.tune = ctx->force_tune ? *ctx->force_tune : lookup_tuning(ctx, prec, sh.n, d);
+  sh.P = choose_chunks(sh.np / 128, sh.np / (tc ? 256 : 128), ctx->sm_count, sh.tune.sim_chunks);
   // The recheck covers an unknown, usually small, set of rows: many short chunks keep every SM busy.
   sh.P3 = int(std::min<int64_t>(32, sh.np / 256));
   // Capacity of a propagation layer: sum over rows of ub_i <= min(n, sum_j len_j).
@@ -624,7 +636,10 @@ rerank_status rerank_create(rerank_ctx** out, const rerank_config* cfg) {
   rerank_ctx* ctx = new (std::nothrow) rerank_ctx();
   if (!ctx) return RERANK_ENOMEM;
   ctx->cfg = *cfg;
-  if (cfg->autotune_path) ctx->tune_path = cfg->autotune_path;
+  if (cfg->autotune_path) {
+    ctx->tune_path = cfg->autotune_path;
+    read_tune_file(ctx->tune_path, &ctx->tune_table);  // a missing file is an empty table
+  }
   ctx->cfg.autotune_path = nullptr;
   ctx->device = cfg->device;
   ctx->sm_count = prop.multiProcessorCount;

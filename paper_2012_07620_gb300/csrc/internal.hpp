@@ -34,12 +34,20 @@ struct Carver {
   }
 };
 
-// Launch shapes chosen per (n, d) by the autotuner or its defaults.
+// Launch shapes chosen per (precision, d, n) by the autotuner or its defaults.
+// None of them changes a result: only which thread computes what, and when.
 struct Tuning {
-  int sim_chunks = 0;      // column chunks P of the similarity top-K kernel (0 = from SM count)
+  int sim_chunks = 0;      // column chunks P of the similarity top-K kernel (0 = from the SM count)
   int prop_warps = 8;      // warps per CTA of the propagation kernel
+  int refine_order = 1;    // 1: refine rows cluster by cluster, 0: in index order
   int rank_threads = 1024; // threads per CTA of the final ranking kernel
 };
+struct TuneEntry {
+  int precision = 0, d = 0, n_bucket = 0;
+  Tuning t;
+  double ms = 0.0;  // pipeline time measured with this entry
+};
+int tune_bucket(int64_t n);  // half-octave bucket of the vertex count
 
 // Device pointers of one pipeline run (all inside the workspace block).
 struct Buffers {
@@ -126,6 +134,7 @@ struct Shape {
   int hash_slots = 0;      // slots of each global hash table (big-row path)
   int rank_ctas = 0;
   int64_t rank_scratch_per_cta = 0;
+  Tuning tune;             // launch shapes of this instance
 };
 
 struct ServeHandle;  // the request loop of a loaded gallery (serve.cu)
@@ -149,7 +158,8 @@ struct rerank_ctx {
   size_t ws_bytes = 0;
   long long* d_status = nullptr;  // device status block (rr::kStCount int64)
   long long* h_status = nullptr;  // pinned host copy
-  rr::Tuning tune{};
+  std::vector<rr::TuneEntry> tune_table;  // loaded from / written to tune_path
+  const rr::Tuning* force_tune = nullptr;  // set while the autotuner measures a candidate
   std::string tune_path;
   int64_t cap_h_hint = 0;      // layer-buffer capacity learned from earlier overflows
   int64_t test_cap_h = 0;      // initial layer capacity forced by RERANK_TEST_CAP_H (tests only)
@@ -259,6 +269,10 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
 rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches);
 rerank_status map_status(const long long* h, int precision, rerank_info* info, int64_t* need);
 int launch_status_reset(long long* st, cudaStream_t s);
+// Tuning of an instance: the table entry for (precision, d, bucket of n), else defaults.
+Tuning lookup_tuning(const rerank_ctx* ctx, int precision, int64_t n, int d);
+bool read_tune_file(const std::string& path, std::vector<TuneEntry>* out);
+bool write_tune_file(const std::string& path, const std::vector<TuneEntry>& entries);
 // Stop the request loop of a loaded gallery and free it (no-op without one).
 rerank_status serve_stop(rerank_ctx* ctx);
 int propagate_warp_slots();

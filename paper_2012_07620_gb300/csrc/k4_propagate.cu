@@ -89,7 +89,9 @@ __device__ __forceinline__ int next_pow2(int x) {
   return p;
 }
 
-__global__ void __launch_bounds__(256)
+constexpr int kMaxPropWarps = 24;  // 24 warps x 8 KB of tables: 192 KB, one CTA per SM
+
+__global__ void __launch_bounds__(kMaxPropWarps * kWarp)
 k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen, const int32_t* __restrict__ scol,
              const float* __restrict__ sval, const int32_t* __restrict__ nbr, const float* __restrict__ nbr_w,
              const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ ub,
@@ -304,7 +306,7 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
   k4_ub<<<unsigned((n + T - 1) / T), T, 0, s>>>(b.nbr, b.nbr_n, k2p1, b.len[src], n, b.ub, b.big_rows, b.big_count,
                                                  status);
   launch_scan(b.ub, n, b.start[dst], s);
-  const int warps = t.prop_warps;
+  const int warps = t.prop_warps < 1 ? 1 : (t.prop_warps > kMaxPropWarps ? kMaxPropWarps : t.prop_warps);
   const size_t smem = size_t(warps) * WSLOTS * 2 * sizeof(int);
   cudaFuncSetAttribute(k4_spmm_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const int64_t blocks_needed = (n + warps - 1) / warps;

@@ -372,7 +372,7 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   em.np = v.rowstride;
   em.eps = (v.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
   // 2. query rows against X_u; gallery rows against the queries
-  const int pa = choose_chunks((Q + 127) / 128, sh.np / 256, sm, ctx->tune.sim_chunks);
+  const int pa = choose_chunks((Q + 127) / 128, sh.np / 256, sm, sh.tune.sim_chunks);
   const int pb = int((Q + 255) / 256);
   char* xl = static_cast<char*>(b.xlow);
   if (launch_sim_tc_rect_topk(sh, xl, Q, 0, xl, n, 0, pa, fp8, b.xscale, sl.floor_a, sl.pa_s, sl.pa_i, status, sm,
@@ -412,13 +412,13 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   int src = 2;
   for (int l = 0; l < v.layers; ++l) {
     const int dst = l & 1;
-    launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, sm, ctx->tune, s);
+    launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, sm, sh.tune, s);
     src = dst;
   }
   launch_row_norms(sh, b, src, status, s);
   int32_t* oi = host_out ? b.out_idx : rq.out_idx;
   float* od = host_out ? b.out_dist : rq.out_dist;
-  launch_rank(sh, b, src, oi, od, status, sm, ctx->tune, s);
+  launch_rank(sh, b, src, oi, od, status, sm, sh.tune, s);
   if (host_out) {
     const size_t cnt = size_t(Q) * size_t(topk);
     RR_CUDA(cudaMemcpyAsync(rq.out_idx, b.out_idx, cnt * 4, cudaMemcpyDeviceToHost, s));

@@ -71,6 +71,11 @@ class ServeInfo(ctypes.Structure):
                 ("slot_bytes", ctypes.c_int64)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("sim_chunks", ctypes.c_int), ("prop_warps", ctypes.c_int), ("refine_order", ctypes.c_int),
+                ("n_bucket", ctypes.c_int), ("ms", ctypes.c_double)]
+
+
 class RerankError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -96,6 +101,11 @@ _SIGS = {
     "rerank_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(TicketInfo)]),
     "rerank_serve_info_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ServeInfo)]),
     "rerank_gallery_unload": (ctypes.c_int, [ctypes.c_void_p]),
+    "rerank_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(Tuning), ctypes.c_void_p]),
+    "rerank_tuning_lookup": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                            ctypes.POINTER(Tuning)]),
     "rerank_knn": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rerank_last_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(RerankInfo)]),
@@ -134,6 +144,17 @@ def check_args(nq, ng, d, dtype, k1, k2, layers, topk_out) -> int:
     """Host-only argument validation (``rerank_check_args``); returns the status code."""
     return load_library().rerank_check_args(nq, ng, d, DTYPE[dtype] if isinstance(dtype, str) else dtype,
                                             k1, k2, layers, topk_out)
+
+
+def tuning_lookup(path: str, precision: str, n: int, d: int) -> Optional[dict]:
+    """Host-only read of a tuning table file (``rerank_tuning_lookup``); None when
+    the file has no entry for (precision, d, bucket of n)."""
+    t = Tuning()
+    st = load_library().rerank_tuning_lookup(path.encode(), PRECISION[precision], n, d, ctypes.byref(t))
+    if st == 8:
+        return None
+    _check(st, "rerank_tuning_lookup")
+    return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
 
 def _check(status: int, where: str) -> None:
@@ -258,6 +279,15 @@ class Reranker:
         self.batch_status = [arr[i].status for i in range(len(jobs))]
         _check(st, "rerank_run_batch")
         return outs
+
+    def autotune(self, xq, xg, k1: int, k2: int, layers: int, stream=None) -> dict:
+        """Measure launch shapes on this instance and keep the best (``rerank_autotune``)."""
+        nq, d = xq.shape
+        ng = xg.shape[0]
+        t = Tuning()
+        _check(self._lib.rerank_autotune(self._h, _ptr(xq), nq, _ptr(xg), ng, d, _dtype_code(xq), k1, k2, layers,
+                                         ctypes.byref(t), _stream_handle(stream)), "rerank_autotune")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
 
     # ---- serving ----
     def load_gallery(self, xg, max_query: int, k1: int, k2: int, layers: int, slots: int = 0) -> None:

@@ -63,3 +63,45 @@ def test_create_without_gpu_reports_status(lib):
     with pytest.raises(rerank.RerankError) as e:
         rerank.Reranker(device=0)
     assert e.value.status == 4  # ECUDA, not a crash
+
+
+def _bucket(n):
+    # the largest b with 2^b <= n^2 (half-octave bucket of the vertex count)
+    b = 0
+    while 2 ** (b + 1) <= n * n:
+        b += 1
+    return b
+
+
+def test_tuning_table_lookup(lib, tmp_path):
+    """The autotuner's JSON table: entries found by (precision, d, bucket of N)."""
+    path = tmp_path / "tune.json"
+    n = 23100
+    path.write_text('{"version": 1, "entries": [\n'
+                    f'  {{"precision": 1, "d": 2048, "n_bucket": {_bucket(n)}, "sim_chunks": 4, "prop_warps": 16, '
+                    '"refine_order": 0, "ms": 7.5},\n'
+                    '  {"precision": 0, "d": 128, "n_bucket": 19, "sim_chunks": 2, "prop_warps": 8, '
+                    '"refine_order": 1, "ms": 0.3}\n]}\n')
+    t = rerank.tuning_lookup(str(path), "bf16", n, 2048)
+    assert t == {"sim_chunks": 4, "prop_warps": 16, "refine_order": 0, "n_bucket": _bucket(n), "ms": 7.5}
+    assert rerank.tuning_lookup(str(path), "bf16", int(n * 0.97), 2048)["sim_chunks"] == 4  # same half-octave
+    assert rerank.tuning_lookup(str(path), "bf16", n * 2, 2048) is None
+    assert rerank.tuning_lookup(str(path), "fp8", n, 2048) is None
+    assert rerank.tuning_lookup(str(path), "fp32", 1000, 128)["prop_warps"] == 8  # 2 log2(1000) = 19.93
+    with pytest.raises(rerank.RerankError):
+        rerank.tuning_lookup(str(tmp_path / "missing.json"), "bf16", n, 2048)
+    bad = tmp_path / "bad.json"
+    bad.write_text("not a table")
+    with pytest.raises(rerank.RerankError):
+        rerank.tuning_lookup(str(bad), "bf16", n, 2048)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 1000, 1023, 1024, 1025, 1448, 1449, 23100, 50000, 2 ** 20, 3 ** 13])
+def test_tuning_bucket_boundaries(lib, tmp_path, n):
+    """The library's bucket is floor(2 log2 N): 2^b <= N^2 < 2^(b+1)."""
+    b = _bucket(n)
+    assert 2 ** b <= n * n < 2 ** (b + 1)
+    path = tmp_path / "t.json"
+    path.write_text('{"entries": [{"precision": 1, "d": 64, "n_bucket": %d, "sim_chunks": 3, "prop_warps": 4, '
+                    '"refine_order": 1}]}' % b)
+    assert rerank.tuning_lookup(str(path), "bf16", n, 64)["n_bucket"] == b
