@@ -5,16 +5,22 @@ features drawn as 1,501 clustered identities plus 2,000 distractors
 (synthetic stand-ins for Market-1501), k1 = 26, k2 = 7, 2 layers, full
 ranked lists (every gallery index per query).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16|fp8]
-                  [--impl ours|reference] [--workload market|large50k|tiny]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp8|fp32]
+                  [--impl ours|reference] [--workload market|large50k|tiny|batched64|serving]
 
-Prints one JSON line.  `value` is ms per re-rank with inputs resident in HBM,
-timed with CUDA events on the launching stream, L2 flushed before every step;
-`e2e` is the same through the C ABI with pinned host buffers (copies inside
-the timed region).  With N > 1 (torchrun) every rank runs an independent
-replica (the method needs no exchange between instances), the time is the
-max over ranks and `value` divides it by all ranks' re-ranks.
-`--impl reference` times the FP64 oracle on the host cores instead.
+Prints one JSON line.  `value` is ms per re-rank with inputs resident in HBM
+on the BF16 tensor-core path (FP32 rescoring, exact neighbour lists), timed
+with CUDA events on the launching stream, L2 flushed before every step;
+`fp32_path` is the plain FP32 path on the same instance; `e2e` is the same
+re-rank through the C ABI with pinned host buffers (copies inside the timed
+region); `serving` is a short Poisson session (200 req/s) against the
+resident 40k-vector gallery with its p50/p99 latency.  `--workload
+batched64` times 64 independent instances per rerank_run_batch call against
+64 sequential calls; `--workload serving` runs the full 60 s session.
+With N > 1 (torchrun) every rank runs an independent replica (the method
+needs no exchange between instances), the time is the max over ranks and
+`value` divides it by all ranks' re-ranks.  `--impl reference` times the
+FP64 oracle on the host cores instead.
 """
 from __future__ import annotations
 
@@ -191,6 +197,34 @@ def _config(args, w):
                         f"L={WORKLOADS[args.workload]['layers']}, full ranked lists",
             "n_vertices": spec.n, "dim": spec.dim, "precision": args.precision,
             "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+
+
+# DRAM bytes (read + write) of one similarity launch, from `ncu --set full` captures
+# (profiles/k1_tc_topk_bf16_market_23k_d2048.md); None where no capture of the
+# current kernel exists.
+SIM_TRAFFIC_BYTES = {("bf16", "market"): 826.9e6}
+
+
+def _roofline(precision, sim_ms, n, d, workload):
+    """Roofline of the dominant kernel, the similarity GEMM with its fused top-K:
+    2 n^2 d flops per launch (the full square; the kernel computes every tile)."""
+    peaks, which = _peaks()
+    flops = 2.0 * n * n * d
+    achieved = flops / (sim_ms * 1e-3) / 1e12
+    if precision == "fp32":
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x {mhz} MHz (derived)"}
+    else:
+        peak = peaks["bf16_tflops"] * (2.0 if precision == "fp8" else 1.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"{which} bf16 burst" + (" x2 (fp8 nominal ratio)" if precision == "fp8" else "")}
+    roof["frac"] = achieved / peak
+    roof["traffic"] = SIM_TRAFFIC_BYTES.get((precision, workload))
+    roof["kernel"] = "similarity_topk (k1_tc_topk / k1_sim_fp32)"
+    roof["flops_per_launch"] = flops
+    return roof
 
 
 def run_batched(args, world, rank, local):
@@ -439,21 +473,8 @@ def run_ours(args, world, rank, local):
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     e2e_ms = _max_over_ranks(e2e_ms, world) / world
 
-    peaks, which = _peaks()
     n = nq + ng
-    sim_ms = stages.get("similarity_topk", float("nan"))
-    flops = 2.0 * n * n * d
-    if args.precision == "fp32":
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": flops / (sim_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0)} MHz"}
-    else:
-        peak = peaks["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
-        roof = {"bound": "tensor", "achieved": flops / (sim_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"{which} bf16 burst" + (" x2 (fp8 nominal ratio)" if args.precision == "fp8" else "")}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["kernel"] = "similarity_topk"
+    roof = _roofline(args.precision, stages.get("similarity_topk", float("nan")), n, d, args.workload)
 
     line = {"metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms * world, "higher_is_better": False, "scaling": "weak",
@@ -467,12 +488,41 @@ def run_ours(args, world, rank, local):
     line["fp64_rescored"] = info["fp64_rescored"]
     line["fallback_rows"] = info["fallback_rows"]
     line["exact_scan_rows"] = info["exact_scan_rows"]
+    R.close()
+    if args.precision != "fp32" and not args.no_fp32_path:
+        # The plain FP32 path on the same instance, for the FP32-vs-BF16 comparison.
+        F = rerank.Reranker(device=local, precision="fp32", stage_timing=True)
+        for _ in range(args.warmup):
+            F.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
+        fsteps = max(1, min(args.steps, 5))
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(fsteps)]
+        fst = {}
+        torch.cuda.synchronize()
+        for k in range(fsteps):
+            flush.fill_(k & 255)
+            fev[k][0].record(stream)
+            F.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
+            fev[k][1].record(stream)
+            for a, v in F.stage_times().items():
+                fst[a] = fst.get(a, 0.0) + v / fsteps
+        torch.cuda.synchronize()
+        fms = sum(a.elapsed_time(b) for a, b in fev) / fsteps
+        line["fp32_path"] = {"ms": fms, "stages_ms": fst,
+                             "roofline": _roofline("fp32", fst.get("similarity_topk", float("nan")), n, d,
+                                                   args.workload),
+                             "bf16_speedup": fms / ms}
+        F.close()
+    if rank == 0 and args.serve_seconds_default > 0 and args.workload == "market":
+        try:
+            line["serving"] = serving_session(rerank, synthetic, dev, args.serve_seconds_default,
+                                              precision=args.precision if args.precision != "fp32" else "bf16")
+        except Exception as e:  # reported, never fatal for the headline line
+            line["serving"] = {"error": repr(e)}
     if rank == 0 and not args.no_cpu_baseline:
         v, sample, threads = cpu_oracle_sample(w.xq, w.xg, k1, target_s=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": threads, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(line))
-    R.close()
 
 
 def main():
@@ -481,11 +531,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp8"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--workload", default="market", choices=list(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-seconds-default", type=float, default=10.0,
+                    help="length of the serving session added to the market line (0 = none)")
+    ap.add_argument("--no-fp32-path", action="store_true")
     args = ap.parse_args()
     world, rank, local = _dist_setup()
     if args.impl == "reference":
