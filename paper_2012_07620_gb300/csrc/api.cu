@@ -405,9 +405,15 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
   K = std::min<int64_t>(K, kmax);
   sh.K = int(K);
   sh.tune = ctx->force_tune ? *ctx->force_tune : lookup_tuning(ctx, prec, sh.n, d);
-  sh.P = choose_chunks(sh.np / 128, sh.np / (tc ? 256 : 128), ctx->sm_count, sh.tune.sim_chunks);
+  // P counts candidate lists per row: one per column chunk on the FP32 path; the
+  // tensor-core kernel writes tc_lists_per_chunk() per chunk, and the refinement
+  // merges at most 32 lists.
+  const int lpc = tc ? tc_lists_per_chunk(sh.dp, 1) : 1;
+  const int lpc3 = tc ? tc_lists_per_chunk(sh.dp, 3) : 1;
+  const int chunks = choose_chunks(sh.np / 128, sh.np / (tc ? 256 : 128), ctx->sm_count, sh.tune.sim_chunks);
+  sh.P = std::min(chunks, 32 / lpc) * lpc;
   // The recheck covers an unknown, usually small, set of rows: many short chunks keep every SM busy.
-  sh.P3 = int(std::min<int64_t>(32, sh.np / 256));
+  sh.P3 = tc ? int(std::min<int64_t>(32 / lpc3, sh.np / 256)) * lpc3 : 0;
   // Capacity of a propagation layer: sum over rows of ub_i <= min(n, sum_j len_j).
   // n^2 bounds it exactly for small graphs; otherwise a generous guess, grown on overflow.
   int64_t guess = std::max<int64_t>(2 * sh.n * k1, std::min<int64_t>(sh.n * sh.n, sh.n * int64_t(k2 + 1) * 160));

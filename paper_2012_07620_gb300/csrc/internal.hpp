@@ -229,6 +229,9 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
                    long long* status, cudaStream_t s, int64_t grid_rows = -1);  // grid_rows: bound on the row count
 size_t tc_smem_bytes();
 int tc_kmax();
+// Candidate lists per row and column chunk written by the tensor-core kernels
+// (their epilogue warp groups) for K depth dp and `segs` products per k-block.
+int tc_lists_per_chunk(int dp, int segs);
 int launch_refine_fallback(const Shape& sh, const void* xq, const void* xg, const float* xhat,
                             const double* norm, int32_t* knn_idx, float* knn_score,
                             const int32_t* fb_rows, const int32_t* fb_count, float* scratch_s,

@@ -45,7 +45,12 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = TBM * 128;    // one 128-byte swizzle row per operand row
 constexpr int B_BYTES = TBN * 128;
 constexpr int KLIST = 64;  // largest candidate list the kernel supports
-constexpr int THREADS = 192;
+// Epilogue warp groups: group g owns columns [g, g+1) * TBN / EG of every tile
+// and keeps its own list per row (EG lists per row and chunk).  Two groups
+// when the MMA work per tile is short (K depth <= 1024), so that the
+// epilogue keeps pace; one otherwise (fewer, longer lists).
+constexpr int EG_MAX = 2;
+constexpr int threads_of(int eg) { return 64 + 128 * eg; }  // TMA warp, MMA warp, 4 epilogue warps per group
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2 };
@@ -53,7 +58,7 @@ enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2 };
 struct alignas(1024) TcSmem {
   uint8_t a[STAGES][A_BYTES];
   uint8_t b[STAGES][B_BYTES];
-  float batch[32][TBM];   // scores of the 32 columns being folded in
+  float batch[EG_MAX][32][TBM];  // per group: scores of the 32 columns being folded in
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
   uint64_t tfull[2];
@@ -87,13 +92,9 @@ __device__ __forceinline__ void item_range(const TcArgs& A, int row_blocks, int 
   t1 = int(int64_t(chunk + 1) * A.col_tiles / A.chunks);
 }
 
-// Packed ordering key of a (score, column) pair: larger = better.
-__device__ __forceinline__ long long pack_key(float s, int col) {
-  return (static_cast<long long>(score_key(s)) << 32) | static_cast<long long>(uint32_t(0x7FFFFFFF - col));
-}
 
-template <int MODE, int KL>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int MODE, int KL, int EGROUPS>
+__global__ void __launch_bounds__(threads_of(EGROUPS), 1)
 k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
            const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs A) {
   extern __shared__ uint8_t smem_raw[];
@@ -113,7 +114,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&sm.tfull[b], 1);
-      tc::mbar_init(&sm.tempty[b], 4);
+      tc::mbar_init(&sm.tempty[b], 4 * EGROUPS);
     }
     tc::mbar_init(&sm.done, 1);
     sm.abort = 0;
@@ -228,27 +229,35 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       tc::mbar_wait(&sm.done, 0, abort, WAIT_LIMIT);
     }
   } else {
-    // ---------------- epilogue: warps 2..5 ----------------
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    // ---------------- epilogue: warps 2 .. 2 + 4 EGROUPS ----------------
+    // Warp w may read TMEM lanes 32 (w % 4) .. + 31 (its rows); the groups split
+    // the tile's columns, and each keeps its own list per row (EGROUPS lists per chunk).
+    const int q = warp & 3;
+    const int eg = (warp - 2) >> 2;
     const int r = q * 32 + lane;
     const uint32_t tlane = tmem + (uint32_t(q * 32) << 16);
     uint32_t tcount = 0;
     bool ok = true;
-    long long lk[KL];
+    // This row's best KL columns of the current chunk: scores ls (descending)
+    // and columns li, in registers.  Columns arrive in increasing order, so a
+    // new column beats a slot only with a strictly larger score: an equal
+    // score keeps the earlier, lower column in front (score desc, column asc).
+    float ls[KL];
+    int li[KL];
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
       int rb, chunk, t0, t1;
       item_range(A, row_blocks, item, rb, chunk, t0, t1);
       const int64_t arow = int64_t(rb) * TBM + r;   // row of the A operand
       const bool live = arow < nrows;
       const int64_t grow = MODE == MODE_SPLIT ? (live ? int64_t(A.rows[arow]) : -1) : A.row0 + arow;  // vertex
-      // This row's best KL columns so far in registers, as packed keys
-      // (score_key << 32 | (INT_MAX - column)): a larger key is a better
-      // column (score desc, column asc).  Sorted descending; empty slots hold
-      // INT64_MIN, which every real column beats.  Admission: beat the last
-      // slot and reach the floor left by chunks of this row that finished earlier.
 #pragma unroll
-      for (int j = 0; j < KL; ++j) lk[j] = LLONG_MIN;
-      const float floor_s = live ? key_score(A.row_floor[arow]) : FLT_MAX;
+      for (int j = 0; j < KL; ++j) {
+        ls[j] = -FLT_MAX;
+        li[j] = kInvalidIdx;
+      }
+      // Admission: beat the last slot and reach the floor left by chunks of
+      // this row that finished earlier (s >= floor, i.e. s > the float below it).
+      const float floor_below = live ? nextafterf(key_score(A.row_floor[arow]), -INFINITY) : INFINITY;
       const float rinv = (MODE == MODE_FP8 && live) ? A.inv_scale[grow] : 1.0f;
       for (int ct = t0; ct < t1; ++ct) {
         const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
@@ -258,50 +267,54 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
         }
         tc::tc_fence_after();
 #pragma unroll 1
-        for (int cb = 0; cb < TBN / 32; ++cb) {
+        for (int cb = eg * (TBN / 32 / EGROUPS); cb < (eg + 1) * (TBN / 32 / EGROUPS); ++cb) {
           uint32_t v[32];
           tc::tmem_ld32(tlane + ab * TBN + cb * 32, v);
           tc::tmem_wait_ld();
-          // Admission test of the 32 columns against the last slot, then a
-          // warp-convergent drain: every round each lane inserts at most one
-          // admitted column with a branch-free pass over its list, so the
-          // warp pays per round, not per column.
+          // Admission test of the 32 columns, then a warp-convergent drain:
+          // every round each lane inserts at most one admitted column with a
+          // branch-free pass over its list, so the warp pays per round.
           const int64_t lbase = int64_t(ct) * TBN + cb * 32;  // B column
           const int64_t cbase = A.col0 + lbase;                // its vertex
-          const long long thr = lk[KL - 1];
+          const int nvalid = int(tmin<int64_t>(A.n - lbase, 32));
+          const int64_t dself = grow - cbase;
+          const int jself = (dself >= 0 && dself < 32) ? int(dself) : -1;
+          const float thr = fmaxf(ls[KL - 1], floor_below);
           uint32_t mask = 0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int64_t col = cbase + j;
-            const bool valid = lbase + j < A.n;
             float s = __uint_as_float(v[j]);
-            if (MODE == MODE_FP8) s = s * rinv * __ldg(A.inv_scale + (valid ? col : 0));
-            if (col == grow) s = 1.0f;
-            sm.batch[j][r] = s;
-            const bool adm = live && valid && s >= floor_s && pack_key(s, int(col)) > thr;
-            mask |= adm ? (1u << j) : 0u;
+            if (MODE == MODE_FP8) s = s * rinv * __ldg(A.inv_scale + (j < nvalid ? cbase + j : 0));
+            if (j == jself) s = 1.0f;
+            if (j >= nvalid) s = -INFINITY;
+            sm.batch[eg][j][r] = s;
+            mask |= (s > thr) ? (1u << j) : 0u;
           }
           int rounds = __popc(mask);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(kFull, rounds, o));
 #pragma unroll 1
           for (int rd = 0; rd < rounds; ++rd) {
-            long long c = LLONG_MIN;
+            float cs = -INFINITY;
+            int ci = kInvalidIdx;
             if (mask) {
               const int j = __ffs(mask) - 1;
               mask &= mask - 1u;
-              c = pack_key(sm.batch[j][r], int(cbase + j));
+              cs = sm.batch[eg][j][r];
+              ci = int(cbase + j);
             }
-            // Insert c into the descending list: slot j takes c where c first
-            // beats lk[j], and lk[j-1] for every later slot.  All comparisons
-            // use the old list, so the pass has no serial dependency.
-            uint64_t beat = 0;
+            // Insert (cs, ci): slot j takes cs where cs first beats ls[j], and
+            // slot j-1's old entry for every later slot.  For the sorted scores
+            // that is max(min(ls[j-1], cs), ls[j]); the columns follow the same
+            // choice.  All tests use the old list: no serial dependency.
 #pragma unroll
-            for (int j = 0; j < KL; ++j) beat |= uint64_t(c > lk[j]) << j;
-#pragma unroll
-            for (int j = KL - 1; j > 0; --j)
-              lk[j] = ((beat >> j) & 1u) ? (((beat >> (j - 1)) & 1u) ? lk[j - 1] : c) : lk[j];
-            lk[0] = (beat & 1u) ? c : lk[0];
+            for (int j = KL - 1; j > 0; --j) {
+              const bool bj = cs > ls[j], bp = cs > ls[j - 1];
+              li[j] = bp ? li[j - 1] : (bj ? ci : li[j]);
+              ls[j] = fmaxf(fminf(ls[j - 1], cs), ls[j]);
+            }
+            li[0] = cs > ls[0] ? ci : li[0];
+            ls[0] = fmaxf(cs, ls[0]);
           }
         }
         tc::tc_fence_before();
@@ -311,21 +324,20 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       }
       if (!ok) break;
       if (live) {
-        const size_t o = (size_t(arow) * A.chunks + chunk) * A.K;
-        // The K-th best as a running minimum over the first K slots: written
-        // this way (not lk[K-1]) so that the list is never indexed dynamically
-        // and stays in registers.
-        long long kth = LLONG_MAX;
+        const size_t o = ((size_t(arow) * A.chunks + chunk) * EGROUPS + eg) * A.K;
+        // The K-th best as a running minimum over the first K slots (the list
+        // is never indexed dynamically, so it stays in registers).
+        float kth = FLT_MAX;
 #pragma unroll
         for (int j = 0; j < KL; ++j) {
           if (j < A.K) {
-            A.part_s[o + j] = lk[j] == LLONG_MIN ? -FLT_MAX : key_score(int(lk[j] >> 32));
-            A.part_i[o + j] = lk[j] == LLONG_MIN ? kInvalidIdx : int(0x7FFFFFFF - int(lk[j] & 0xFFFFFFFF));
+            A.part_s[o + j] = ls[j];
+            A.part_i[o + j] = li[j];
+            kth = fminf(kth, ls[j]);
           }
-          if (j < A.K) kth = lk[j] < kth ? lk[j] : kth;
         }
         // This chunk's K-th best becomes a floor for the row's later chunks.
-        if (kth != LLONG_MIN && kth != LLONG_MAX) atomicMax(A.row_floor + arow, int(kth >> 32));
+        if (kth != -FLT_MAX) atomicMax(A.row_floor + arow, score_key(kth));
       }
     }
     if (!ok) {
@@ -369,22 +381,29 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int dp, bool fp8
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int MODE, int KL>
+template <int MODE, int KL, int EG>
 void launch_kl(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
                const TcArgs& A, int grid, cudaStream_t s) {
   const size_t smem = sizeof(TcSmem) + 1024;
-  cudaFuncSetAttribute(k1_tc_topk<MODE, KL>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  k1_tc_topk<MODE, KL><<<grid, THREADS, smem, s>>>(a0, a1, b0, b1, A);
+  cudaFuncSetAttribute(k1_tc_topk<MODE, KL, EG>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  k1_tc_topk<MODE, KL, EG><<<grid, threads_of(EG), smem, s>>>(a0, a1, b0, b1, A);
 }
 
 // The per-row list lives in registers, so its length is a compile-time choice.
 template <int MODE>
 void launch_mode(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
-                 const TcArgs& A, int grid, cudaStream_t s) {
-  if (A.K <= 48)
-    launch_kl<MODE, 48>(a0, a1, b0, b1, A, grid, s);
-  else
-    launch_kl<MODE, KLIST>(a0, a1, b0, b1, A, grid, s);
+                 const TcArgs& A, int eg, int grid, cudaStream_t s) {
+  if (A.K <= 48) {
+    if (eg == 2)
+      launch_kl<MODE, 48, 2>(a0, a1, b0, b1, A, grid, s);
+    else
+      launch_kl<MODE, 48, 1>(a0, a1, b0, b1, A, grid, s);
+  } else {
+    if (eg == 2)
+      launch_kl<MODE, KLIST, 2>(a0, a1, b0, b1, A, grid, s);
+    else
+      launch_kl<MODE, KLIST, 1>(a0, a1, b0, b1, A, grid, s);
+  }
 }
 
 __global__ void k_gather_rows(const int32_t* __restrict__ rows, const int32_t* __restrict__ count,
@@ -403,6 +422,8 @@ __global__ void k_gather_rows(const int32_t* __restrict__ rows, const int32_t* _
 }  // namespace
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
+int tc_lists_per_chunk(int dp, int segs) { return dp * segs <= 1024 ? 2 : 1; }
+static_assert(sizeof(TcSmem) + 1024 <= 227 * 1024, "shared memory of the tensor-core kernel");
 int tc_kmax() { return KLIST; }
 int tc_tile_rows() { return TBM; }
 int tc_tile_cols() { return TBN; }
@@ -419,7 +440,9 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   A.a_rows = sh.n;
   A.row_blocks = int(sh.np / TBM);
   A.col_tiles = int(sh.np / TBN);
-  A.chunks = sh.P;
+  const int eg = tc_lists_per_chunk(sh.dp, 1);
+  A.chunks = sh.P / eg;  // sh.P counts lists per row
+  if (A.chunks < 1 || A.chunks * eg != sh.P || A.chunks > A.col_tiles) return -1;
   A.kblocks = fp8 ? sh.dp / 128 : sh.dp / 64;
   A.K = sh.K;
   A.inv_scale = inv_scale;
@@ -430,9 +453,9 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   const int items = A.row_blocks * A.chunks;
   const int grid = items < sm_count ? items : sm_count;
   if (fp8)
-    launch_mode<MODE_FP8>(map, map, map, map, A, grid, s);
+    launch_mode<MODE_FP8>(map, map, map, map, A, eg, grid, s);
   else
-    launch_mode<MODE_BF16>(map, map, map, map, A, grid, s);
+    launch_mode<MODE_BF16>(map, map, map, map, A, eg, grid, s);
   return 1;
 }
 
@@ -453,8 +476,9 @@ int launch_sim_tc_rect_topk(const Shape& sh, const void* a, int64_t a_rows, int6
   A.col0 = col0;
   A.row_blocks = int((a_rows + TBM - 1) / TBM);
   A.col_tiles = int((b_cols + TBN - 1) / TBN);
-  if (chunks < 1 || chunks > A.col_tiles) return -1;  // the caller reads exactly `chunks` lists per row
+  if (chunks < 1 || chunks > A.col_tiles) return -1;  // the caller reads chunks * tc_lists_per_chunk lists per row
   A.chunks = chunks;
+  const int eg = tc_lists_per_chunk(sh.dp, 1);
   A.kblocks = fp8 ? sh.dp / 128 : sh.dp / 64;
   A.K = sh.K;
   A.inv_scale = inv_scale;
@@ -465,9 +489,9 @@ int launch_sim_tc_rect_topk(const Shape& sh, const void* a, int64_t a_rows, int6
   const int items = A.row_blocks * A.chunks;
   const int grid = items < sm_count ? items : sm_count;
   if (fp8)
-    launch_mode<MODE_FP8>(ma, ma, mb, mb, A, grid, s);
+    launch_mode<MODE_FP8>(ma, ma, mb, mb, A, eg, grid, s);
   else
-    launch_mode<MODE_BF16>(ma, ma, mb, mb, A, grid, s);
+    launch_mode<MODE_BF16>(ma, ma, mb, mb, A, eg, grid, s);
   return 1;
 }
 
@@ -484,7 +508,9 @@ int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, 
   A.n = sh.n;
   A.row_blocks = 0;
   A.col_tiles = int(sh.np / TBN);
-  A.chunks = P3;
+  const int eg = tc_lists_per_chunk(sh.dp, 3);
+  A.chunks = P3 / eg;  // P3 counts lists per row
+  if (A.chunks < 1 || A.chunks * eg != P3 || A.chunks > A.col_tiles) return -1;
   A.kblocks = sh.dp / 64;
   A.K = sh.K;
   A.rows = rows;
@@ -493,7 +519,7 @@ int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, 
   A.part_s = part_s;
   A.part_i = part_i;
   A.status = status;
-  launch_mode<MODE_SPLIT>(a0, a1, b0, b1, A, sm_count, s);
+  launch_mode<MODE_SPLIT>(a0, a1, b0, b1, A, eg, sm_count, s);
   return 1;
 }
 

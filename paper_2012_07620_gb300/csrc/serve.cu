@@ -50,6 +50,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 constexpr int kMaxSlots = 8;
 constexpr int64_t kMaxQuery = 1024;  // query columns of a request: at most 4 tiles of 256
+constexpr int kMaxQueryLists = 8;    // lists per gallery row against the queries: 4 chunks x 2
 constexpr int64_t kPad = 256;  // zero rows after the gallery: one full tensor-core tile
 
 struct Server;
@@ -135,7 +136,7 @@ size_t slot_layout(const Server& v, Slot* sl, char* base, const Shape& shmax, in
   Carver c;
   c.base = base;
   const size_t rows = size_t(v.rowstride), dp = size_t(v.dp);
-  const int pa_max = 32, pb_max = int((v.S + 255) / 256);
+  const int pa_max = 32, pb_max = int((v.S + 255) / 256) * tc_lists_per_chunk(v.dp, 1);
   Slot t;
   t.xhat = c.take<float>(rows * dp);
   t.xlow = c.take<char>(rows * dp * esize(v.prec));
@@ -240,7 +241,7 @@ k_serve_assemble(int64_t G, int64_t Q, int K, int k1, int Pb, const float* __res
   pos = __shfl_sync(kFull, pos, 0);
   if (lane != 0) return;
   // Merge (1 + Pb) sorted lists into the K best by (score desc, index asc).
-  int head[1 + int(kMaxQuery / 256)] = {};
+  int head[1 + kMaxQueryLists] = {};
   const int L = 1 + Pb;
   for (int e = 0; e < K; ++e) {
     int best = -1;
@@ -372,8 +373,9 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   em.np = v.rowstride;
   em.eps = (v.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
   // 2. query rows against X_u; gallery rows against the queries
-  const int pa = choose_chunks((Q + 127) / 128, sh.np / 256, sm, sh.tune.sim_chunks);
-  const int pb = int((Q + 255) / 256);
+  const int lpc = tc_lists_per_chunk(v.dp, 1);
+  const int pa = std::min(choose_chunks((Q + 127) / 128, sh.np / 256, sm, sh.tune.sim_chunks), 32 / lpc);
+  const int pb = int((Q + 255) / 256);  // chunks; the lists per row are lpc times as many
   char* xl = static_cast<char*>(b.xlow);
   if (launch_sim_tc_rect_topk(sh, xl, Q, 0, xl, n, 0, pa, fp8, b.xscale, sl.floor_a, sl.pa_s, sl.pa_i, status, sm,
                               s) < 0)
@@ -384,11 +386,11 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   // 3. resident or re-derived gallery lists
   const double eps_r = rescore_eps(v.dp);
   k_serve_assemble<<<unsigned((G + AWPB - 1) / AWPB), AWPB * kWarp, 0, s>>>(
-      G, Q, v.K, v.k1, pb, v.res_s, v.res_i, v.res_knn_idx, v.res_knn_score, sl.pb_s, sl.pb_i, b.err, sl.emax_q,
+      G, Q, v.K, v.k1, pb * lpc, v.res_s, v.res_i, v.res_knn_idx, v.res_knn_score, sl.pb_s, sl.pb_i, b.err, sl.emax_q,
       em.eps, eps_r, b.knn_idx, b.knn_score, sl.pm_s, sl.pm_i, sl.touched, sl.scal + 1, status);
   // 4. refinement of the query rows and of the touched gallery rows
   const void* dg = v.xg_raw;
-  launch_refine(sh, dq, dg, b.xhat, b.norm, sl.pa_s, sl.pa_i, pa, em, sl.iota, sl.scal, true, b.knn_idx,
+  launch_refine(sh, dq, dg, b.xhat, b.norm, sl.pa_s, sl.pa_i, pa * lpc, em, sl.iota, sl.scal, true, b.knn_idx,
                 b.knn_score, b.fb_rows, b.fb_count, status, s, Q);
   launch_refine(sh, dq, dg, b.xhat, b.norm, sl.pm_s, sl.pm_i, 1, em, sl.touched, sl.scal + 1, false, b.knn_idx,
                 b.knn_score, b.fb_rows, b.fb_count, status, s, G);

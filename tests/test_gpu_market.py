@@ -1,5 +1,5 @@
-"""Full-size workload (3,368 + 19,732 vectors, d = 2048, k1 = 26, k2 = 7, L = 2),
-in the configuration bench.py times.
+"""Full-size workloads: 3,368 + 19,732 vectors, d = 2048 (the configuration
+bench.py times) and 5,000 + 45,000 vectors, d = 512; k1 = 26, k2 = 7, L = 2.
 
 The oracle cannot run the whole pipeline here in seconds, so it checks a
 sample: the exact neighbour lists of 192 sampled rows (Eq. 7-8 in FP64).
@@ -20,12 +20,12 @@ torch = pytest.importorskip("torch")
 K1, K2, L = 26, 7, 2
 
 
-@pytest.fixture(scope="module")
-def market():
+@pytest.fixture(scope="module", params=["MARKET_SCALE", "LARGE_50K"])
+def market(request):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2012_07620_gb300 import rerank
-    w = synthetic.make_workload(synthetic.MARKET_SCALE)
+    w = synthetic.make_workload(getattr(synthetic, request.param))
     xq = torch.from_numpy(w.xq).cuda()
     xg = torch.from_numpy(w.xg).cuda()
     out = {}
