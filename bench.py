@@ -433,8 +433,15 @@ def run_ours(args, world, rank, local):
     out_i = torch.empty((nq, ng), dtype=torch.int32, device=dev)
     out_d = torch.empty((nq, ng), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    R = rerank.Reranker(device=local, precision=args.precision, stage_timing=True)
     stream = torch.cuda.current_stream(dev)
+    tune_path, tuned = None, None
+    if not args.no_autotune:
+        # Launch shapes from the autotuner, measured on this instance before the timed region.
+        tune_path = os.path.join(tempfile.mkdtemp(), "tune.json")
+        T = rerank.Reranker(device=local, precision=args.precision, autotune_path=tune_path)
+        tuned = T.autotune(xq, xg, k1, k2, L)
+        T.close()
+    R = rerank.Reranker(device=local, precision=args.precision, stage_timing=True, autotune_path=tune_path)
 
     for _ in range(args.warmup):
         R.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
@@ -483,7 +490,7 @@ def run_ours(args, world, rank, local):
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(hq.numel() * 4 + hg.numel() * 4),
                     "d2h_bytes_per_step": int(ho_i.numel() * 4 + ho_d.numel() * 4)},
             "roofline": roof, "stages_ms": stages, "gpu_launches": int(launches * args.steps),
-            "clocks": clocks.summary()}
+            "clocks": clocks.summary(), "autotune": tuned}
     info = R.last_info()
     line["fp64_rescored"] = info["fp64_rescored"]
     line["fallback_rows"] = info["fallback_rows"]
@@ -491,7 +498,13 @@ def run_ours(args, world, rank, local):
     R.close()
     if args.precision != "fp32" and not args.no_fp32_path:
         # The plain FP32 path on the same instance, for the FP32-vs-BF16 comparison.
-        F = rerank.Reranker(device=local, precision="fp32", stage_timing=True)
+        ftune = None
+        if not args.no_autotune:
+            ftune = os.path.join(os.path.dirname(tune_path), "tune_fp32.json")
+            T = rerank.Reranker(device=local, precision="fp32", autotune_path=ftune)
+            T.autotune(xq, xg, k1, k2, L)
+            T.close()
+        F = rerank.Reranker(device=local, precision="fp32", stage_timing=True, autotune_path=ftune)
         for _ in range(args.warmup):
             F.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
         fsteps = max(1, min(args.steps, 5))
@@ -539,6 +552,7 @@ def main():
     ap.add_argument("--serve-seconds-default", type=float, default=10.0,
                     help="length of the serving session added to the market line (0 = none)")
     ap.add_argument("--no-fp32-path", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of autotuned ones")
     args = ap.parse_args()
     world, rank, local = _dist_setup()
     if args.impl == "reference":

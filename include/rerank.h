@@ -226,11 +226,15 @@ rerank_status rerank_gallery_unload(rerank_ctx* ctx);
  * decomposition (the paper fixes no schedule; these are GPU choices):
  *   sim_chunks    column chunks of the similarity top-K kernel (0 = SM-count heuristic)
  *   prop_warps    warps per CTA of the propagation kernel
- *   refine_order  1 = refine rows cluster by cluster, 0 = in index order */
+ *   refine_order  1 = refine rows cluster by cluster, 0 = in index order
+ *   rescore_m     candidates kept beyond k1 (-1 = cfg.rescore_m); the lists
+ *                 stay exact for any value, only the work moves between stages.
+ *                 Serving always uses cfg.rescore_m. */
 typedef struct {
   int sim_chunks;
   int prop_warps;
   int refine_order;
+  int rescore_m;
   int n_bucket;
   double ms; /* pipeline time measured with this choice */
 } rerank_tuning;

@@ -65,7 +65,8 @@ int choose_chunks(int64_t row_blocks, int64_t col_tiles, int sm_count, int force
     const int64_t ctas = row_blocks * p;
     const int64_t waves = (ctas + sm_count - 1) / sm_count;
     const int64_t tiles = (col_tiles + p - 1) / p;
-    const double cost = double(waves) * double(tiles) + 0.02 * p;  // small charge for more partial lists
+    // Every chunk starts its lists cold (no floor yet): charge it about three tiles.
+    const double cost = double(waves) * (double(tiles) + 3.0);
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
       best = p;
@@ -380,7 +381,8 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
 
 // Shape of one instance.  cap_hint: a layer capacity learned from an earlier overflow.
 rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, int k1, int k2, int layers,
-                         int64_t topk, bool knn_only, bool host_in, bool host_out, int64_t cap_hint, Shape* out) {
+                         int64_t topk, bool knn_only, bool host_in, bool host_out, int64_t cap_hint, Shape* out,
+                         const Tuning* tune) {
   Shape sh;
   sh.nq = nq;
   sh.ng = ng;
@@ -401,10 +403,11 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
   sh.host_out = host_out;
   const int kmax = std::min(tc ? tc_kmax() : sim_fp32_kmax(), refine_kmax());
   if (k1 > kmax) return RERANK_EUNSUPPORTED;
-  int64_t K = std::min<int64_t>(int64_t(k1) + std::max(ctx->cfg.rescore_m, 0), sh.n);
+  sh.tune = tune ? *tune : (ctx->force_tune ? *ctx->force_tune : lookup_tuning(ctx, prec, sh.n, d));
+  const int m = sh.tune.rescore_m >= 0 ? sh.tune.rescore_m : ctx->cfg.rescore_m;
+  int64_t K = std::min<int64_t>(int64_t(k1) + std::max(m, 0), sh.n);
   K = std::min<int64_t>(K, kmax);
   sh.K = int(K);
-  sh.tune = ctx->force_tune ? *ctx->force_tune : lookup_tuning(ctx, prec, sh.n, d);
   // P counts candidate lists per row: one per column chunk on the FP32 path; the
   // tensor-core kernel writes tc_lists_per_chunk() per chunk, and the refinement
   // merges at most 32 lists.

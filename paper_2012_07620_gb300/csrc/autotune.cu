@@ -8,7 +8,10 @@
 //   prop_warps    warps per CTA of the propagation kernel (one hash table of
 //                 8 KB per warp in shared memory);
 //   refine_order  refine rows cluster by cluster (candidate rows shared in L1)
-//                 or in index order (no ordering pass).
+//                 or in index order (no ordering pass);
+//   rescore_m     candidates kept beyond k1 (K = k1 + m): a longer list costs
+//                 the similarity epilogue and the refinement more, and leaves
+//                 fewer rows uncertified for the hi/lo recheck.
 // The GEMM tile (128 x 256 x 64 bytes of K, 4-stage TMA ring, one CTA per SM)
 // is fixed: it is the largest tile whose accumulators (2 x 256 TMEM columns)
 // and operand ring fit one SM, and the per-row top-K epilogue needs a whole
@@ -21,7 +24,7 @@
 // Table format (written by write_tune_file, read back by read_tune_file):
 //   {"version": 1, "entries": [
 //     {"precision": 1, "d": 2048, "n_bucket": 29, "sim_chunks": 4,
-//      "prop_warps": 8, "refine_order": 1, "ms": 7.05}, ...]}
+//      "prop_warps": 8, "refine_order": 1, "rescore_m": 22, "ms": 6.4}, ...]}
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -87,10 +90,11 @@ bool read_tune_file(const std::string& path, std::vector<TuneEntry>* out) {
     const size_t b = text.find('}', a);
     if (b == std::string::npos) break;
     const std::string obj = text.substr(a, b - a + 1);
-    double prec, d, nb, pc, pw, ro, ms = 0.0;
+    double prec, d, nb, pc, pw, ro, ms = 0.0, rm = -1.0;
     if (field(obj, "precision", &prec) && field(obj, "d", &d) && field(obj, "n_bucket", &nb) &&
         field(obj, "sim_chunks", &pc) && field(obj, "prop_warps", &pw) && field(obj, "refine_order", &ro)) {
       field(obj, "ms", &ms);
+      field(obj, "rescore_m", &rm);
       TuneEntry e;
       e.precision = int(prec);
       e.d = int(d);
@@ -98,6 +102,7 @@ bool read_tune_file(const std::string& path, std::vector<TuneEntry>* out) {
       e.t.sim_chunks = std::max(0, std::min(32, int(pc)));
       e.t.prop_warps = std::max(1, std::min(24, int(pw)));
       e.t.refine_order = ro != 0.0 ? 1 : 0;
+      e.t.rescore_m = std::max(-1, std::min(256, int(rm)));
       e.ms = ms;
       entries.push_back(e);
     }
@@ -116,8 +121,9 @@ bool write_tune_file(const std::string& path, const std::vector<TuneEntry>& entr
     const TuneEntry& e = entries[i];
     std::fprintf(f,
                  "%s\n  {\"precision\": %d, \"d\": %d, \"n_bucket\": %d, \"sim_chunks\": %d, \"prop_warps\": %d, "
-                 "\"refine_order\": %d, \"ms\": %.4f}",
-                 i ? "," : "", e.precision, e.d, e.n_bucket, e.t.sim_chunks, e.t.prop_warps, e.t.refine_order, e.ms);
+                 "\"refine_order\": %d, \"rescore_m\": %d, \"ms\": %.4f}",
+                 i ? "," : "", e.precision, e.d, e.n_bucket, e.t.sim_chunks, e.t.prop_warps, e.t.refine_order,
+                 e.t.rescore_m, e.ms);
   }
   std::fprintf(f, "\n]}\n");
   const bool ok = std::fclose(f) == 0;
@@ -176,6 +182,25 @@ rerank_status rerank_autotune(rerank_ctx* ctx, const void* xq, int64_t nq, const
   best.sim_chunks = 0;
   double best_ms = 0.0;
   do {
+    // 0. candidates kept beyond k1: more cost in the similarity epilogue and
+    //    the refinement, fewer rows left for the recheck
+    {
+      double t0_best = 1e300;
+      const int m_set[] = {-1, 8, 22, 30};
+      Tuning base0 = best;
+      for (int m : m_set) {
+        Tuning t = base0;
+        t.rescore_m = m;
+        double ms = 0.0;
+        st = timed_run(ctx, t, xq, nq, xg, ng, d, dtype, k1, k2, layers, oi, od, stream, nullptr, &ms);
+        if (st != RERANK_OK) break;
+        if (ms < t0_best * 0.99) {
+          t0_best = ms;
+          best.rescore_m = m;
+        }
+      }
+      if (st != RERANK_OK) break;
+    }
     // 1. column chunks of the similarity stage (0 = the SM-count heuristic)
     const int chunk_set[] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
     double t_best = 1e300;
@@ -247,6 +272,7 @@ rerank_status rerank_autotune(rerank_ctx* ctx, const void* xq, int64_t nq, const
     out->sim_chunks = best.sim_chunks;
     out->prop_warps = best.prop_warps;
     out->refine_order = best.refine_order;
+    out->rescore_m = best.rescore_m;
     out->n_bucket = e.n_bucket;
     out->ms = best_ms;
   }
@@ -263,6 +289,7 @@ rerank_status rerank_tuning_lookup(const char* path, int precision, int64_t n, i
       out->sim_chunks = e.t.sim_chunks;
       out->prop_warps = e.t.prop_warps;
       out->refine_order = e.t.refine_order;
+      out->rescore_m = e.t.rescore_m;
       out->n_bucket = nb;
       out->ms = e.ms;
       return RERANK_OK;

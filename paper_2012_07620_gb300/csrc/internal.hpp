@@ -40,6 +40,7 @@ struct Tuning {
   int sim_chunks = 0;      // column chunks P of the similarity top-K kernel (0 = from the SM count)
   int prop_warps = 8;      // warps per CTA of the propagation kernel
   int refine_order = 1;    // 1: refine rows cluster by cluster, 0: in index order
+  int rescore_m = -1;      // candidates kept beyond k1 (-1: the context's cfg.rescore_m)
   int rank_threads = 1024; // threads per CTA of the final ranking kernel
 };
 struct TuneEntry {
@@ -268,7 +269,7 @@ int choose_chunks(int64_t row_blocks, int64_t col_tiles, int sm_count, int force
 size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision);
 rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, int k1, int k2,
                          int layers, int64_t topk, bool knn_only, bool host_in, bool host_out, int64_t cap_hint,
-                         Shape* out);
+                         Shape* out, const Tuning* tune = nullptr);  // tune: override of the table lookup
 rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches);
 rerank_status map_status(const long long* h, int precision, rerank_info* info, int64_t* need);
 int launch_status_reset(long long* st, cudaStream_t s);

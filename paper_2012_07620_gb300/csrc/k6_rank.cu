@@ -207,11 +207,20 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     const int wpw = (nwords + RW - 1) / RW;
     const int w0 = min(nwords, w * wpw), w1 = min(nwords, w0 + wpw);
     int mine = 0;
-    for (int wd = w0; wd < w1; ++wd) {
-      const int64_t g = int64_t(wd) * 32 + lane;
-      const unsigned bal = __ballot_sync(kFull, g < ng && acc[g] != 0u);
-      if (lane == 0) bits[wd] = bal;
-      mine += __popc(bal);
+    // Four words per step: independent loads in flight (the accumulator may live in global memory).
+    for (int wd = w0; wd < w1; wd += 4) {
+      uint32_t x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t g = int64_t(wd + u) * 32 + lane;
+        x[u] = (wd + u < w1 && g < ng) ? acc[g] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned bal = __ballot_sync(kFull, x[u] != 0u);
+        if (lane == 0 && wd + u < w1) bits[wd + u] = bal;
+        mine += __popc(bal);
+      }
     }
     int off;
     const int cnt = block_exscan(lane == 0 ? mine : 0, tmp, off);  // one count per warp (lane 0)
@@ -219,15 +228,22 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     const bool small = cnt <= SORT_CAP && A.acc_smem && ng >= 2 * int64_t(cnt);
     uint32_t* k0 = small ? skeys : gk0;
     uint32_t* v0 = small ? svals : gv0;
-    for (int wd = w0; wd < w1; ++wd) {
-      const unsigned bal = bits[wd];
-      const int64_t g = int64_t(wd) * 32 + lane;
-      if ((bal >> lane) & 1u) {
-        const int pos = off + __popc(bal & lt);
-        k0[pos] = ~acc[g];
-        v0[pos] = uint32_t(g);
+    for (int wd = w0; wd < w1; wd += 4) {
+      uint32_t bal[4], x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
+        x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
       }
-      off += __popc(bal);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if ((bal[u] >> lane) & 1u) {
+          const int pos = off + __popc(bal[u] & lt);
+          k0[pos] = ~x[u];
+          v0[pos] = uint32_t(int64_t(wd + u) * 32 + lane);
+        }
+        off += __popc(bal[u]);
+      }
     }
     __syncthreads();
     uint32_t* k1 = small ? acc : gk1;

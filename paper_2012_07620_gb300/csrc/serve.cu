@@ -327,7 +327,11 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   const int64_t topk = rq.topk_out ? rq.topk_out : G;
   const bool host_out = is_host_ptr(rq.out_idx) || is_host_ptr(rq.out_dist);
   Shape sh;
-  rerank_status st = plan_shape(ctx, Q, G, v.d, v.dtype, v.k1, v.k2, v.layers, topk, false, false, host_out, 0, &sh);
+  // The resident lists were made with the context's rescore_m: requests use it too.
+  Tuning tq = lookup_tuning(ctx, v.prec, G + Q, v.d);
+  tq.rescore_m = -1;
+  rerank_status st =
+      plan_shape(ctx, Q, G, v.d, v.dtype, v.k1, v.k2, v.layers, topk, false, false, host_out, 0, &sh, &tq);
   if (st != RERANK_OK) return st;
   sh.ext_feat = true;
   sh.cap_h = v.cap_h;
@@ -551,7 +555,9 @@ rerank_status serve_load(rerank_ctx* ctx, const void* xg, int64_t ng, int d, int
   v->prec = prec;
   // 1. the gallery's own exact neighbour lists: the rerank_knn pipeline on G
   Shape shg;
-  st = plan_shape(ctx, ng, 0, d, dtype, k1, 1, 0, 0, true, false, false, 0, &shg);
+  Tuning tg = lookup_tuning(ctx, prec, ng, d);
+  tg.rescore_m = -1;
+  st = plan_shape(ctx, ng, 0, d, dtype, k1, 1, 0, 0, true, false, false, 0, &shg, &tg);
   if (st != RERANK_OK) {
     delete v;
     return st;
@@ -559,7 +565,9 @@ rerank_status serve_load(rerank_ctx* ctx, const void* xg, int64_t ng, int d, int
   v->dp = shg.dp;
   v->K = shg.K;
   Shape shmax;
-  st = plan_shape(ctx, S, ng, d, dtype, k1, k2, layers, ng, false, false, true, 0, &shmax);
+  Tuning tm = lookup_tuning(ctx, prec, S + ng, d);
+  tm.rescore_m = -1;
+  st = plan_shape(ctx, S, ng, d, dtype, k1, k2, layers, ng, false, false, true, 0, &shmax, &tm);
   if (st != RERANK_OK) {
     delete v;
     return st;

@@ -73,7 +73,7 @@ class ServeInfo(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("sim_chunks", ctypes.c_int), ("prop_warps", ctypes.c_int), ("refine_order", ctypes.c_int),
-                ("n_bucket", ctypes.c_int), ("ms", ctypes.c_double)]
+                ("rescore_m", ctypes.c_int), ("n_bucket", ctypes.c_int), ("ms", ctypes.c_double)]
 
 
 class RerankError(RuntimeError):

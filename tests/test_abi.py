@@ -81,13 +81,15 @@ def test_tuning_table_lookup(lib, tmp_path):
                     f'  {{"precision": 1, "d": 2048, "n_bucket": {_bucket(n)}, "sim_chunks": 4, "prop_warps": 16, '
                     '"refine_order": 0, "ms": 7.5},\n'
                     '  {"precision": 0, "d": 128, "n_bucket": 19, "sim_chunks": 2, "prop_warps": 8, '
-                    '"refine_order": 1, "ms": 0.3}\n]}\n')
+                    '"refine_order": 1, "rescore_m": 22, "ms": 0.3}\n]}\n')
     t = rerank.tuning_lookup(str(path), "bf16", n, 2048)
-    assert t == {"sim_chunks": 4, "prop_warps": 16, "refine_order": 0, "n_bucket": _bucket(n), "ms": 7.5}
+    assert t == {"sim_chunks": 4, "prop_warps": 16, "refine_order": 0, "rescore_m": -1, "n_bucket": _bucket(n),
+                 "ms": 7.5}
     assert rerank.tuning_lookup(str(path), "bf16", int(n * 0.97), 2048)["sim_chunks"] == 4  # same half-octave
     assert rerank.tuning_lookup(str(path), "bf16", n * 2, 2048) is None
     assert rerank.tuning_lookup(str(path), "fp8", n, 2048) is None
-    assert rerank.tuning_lookup(str(path), "fp32", 1000, 128)["prop_warps"] == 8  # 2 log2(1000) = 19.93
+    t2 = rerank.tuning_lookup(str(path), "fp32", 1000, 128)  # 2 log2(1000) = 19.93
+    assert t2["prop_warps"] == 8 and t2["rescore_m"] == 22
     with pytest.raises(rerank.RerankError):
         rerank.tuning_lookup(str(tmp_path / "missing.json"), "bf16", n, 2048)
     bad = tmp_path / "bad.json"

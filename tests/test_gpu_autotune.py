@@ -61,15 +61,15 @@ def test_autotune_writes_table_and_keeps_results(lib, data, tmp_path, precision)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
-@pytest.mark.parametrize("shape", [(1, 4, 0), (3, 16, 1), (32, 24, 0), (2, 8, 1)])
+@pytest.mark.parametrize("shape", [(1, 4, 0, 8), (3, 16, 1, 22), (32, 24, 0, 30), (2, 8, 1, -1), (0, 8, 1, 1)])
 def test_every_launch_shape_gives_the_same_result(lib, data, tmp_path, precision, shape):
     xq, xg = data
-    chunks, warps, order = shape
+    chunks, warps, order, m = shape
     path = tmp_path / "t.json"
     prec = {"fp32": 0, "bf16": 1, "fp8": 2}[precision]
     path.write_text(json.dumps({"version": 1, "entries": [
         {"precision": prec, "d": SPEC.dim, "n_bucket": _bucket(SPEC.n), "sim_chunks": chunks, "prop_warps": warps,
-         "refine_order": order, "ms": 0}]}))
+         "refine_order": order, "rescore_m": m, "ms": 0}]}))
     with lib.Reranker(precision=precision) as D, lib.Reranker(precision=precision, autotune_path=str(path)) as R:
         a = _run(D, xq, xg)
         b = _run(R, xq, xg)
