@@ -144,19 +144,74 @@ __device__ int merge_lists(WarpSmem& w, const float* ls, const int32_t* li, int 
   return cnt;
 }
 
+// Row i's unit row held in registers (dp <= 128 * RV), so that rescoring
+// reads only the candidates' rows.  Lane l holds float4s l, l + 32, ...
+// Four FP32 dot products with the register-resident row: the same per-lane
+// FMA chains and warp tree as dot2_fp32, so the values are identical.
+template <int RV>
+__device__ __forceinline__ void dot4_reg(const float4 (&xr)[RV], int nv, const float* y0, const float* y1,
+                                         const float* y2, const float* y3, int lane, float (&r)[4]) {
+  const float4* b[4] = {reinterpret_cast<const float4*>(y0), reinterpret_cast<const float4*>(y1),
+                        reinterpret_cast<const float4*>(y2), reinterpret_cast<const float4*>(y3)};
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int t = 0; t < RV; ++t) {
+    if (t < nv) {
+      const float4 x = xr[t];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float4 u = __ldg(b[c] + lane + 32 * t);
+        acc[c] = fmaf(x.x, u.x, acc[c]);
+        acc[c] = fmaf(x.y, u.y, acc[c]);
+        acc[c] = fmaf(x.z, u.z, acc[c]);
+        acc[c] = fmaf(x.w, u.w, acc[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) r[c] = warp_sum(acc[c]);
+}
+
 // Steps 2-5 for row i on candidates w.idx[0..K).  Returns false when the
 // candidate list cannot be certified (then nothing is written unless `last`).
+// RV > 0: keep row i in registers when dp <= 128 RV (the warp-per-row
+// kernel; the fallback's 1024-thread CTAs have no registers to spare).
+template <int RV>
 __device__ bool refine_warp(WarpSmem& w, int K, int64_t i, int k1, float B, double eps_g, double eps_r,
                             const RowIo& io, bool last, int lane) {
   const float* xi = io.xhat + size_t(i) * io.dp;
-  for (int c = 0; c < K; c += 2) {
-    const int j0 = w.idx[c];
-    const int j1 = c + 1 < K ? w.idx[c + 1] : j0;
-    float v0, v1;
-    dot2_fp32(xi, io.xhat + size_t(j0) * io.dp, io.xhat + size_t(j1) * io.dp, io.dp, lane, v0, v1);
-    if (lane == 0) {
-      w.s[c] = j0 == i ? 1.0f : v0;
-      if (c + 1 < K) w.s[c + 1] = j1 == i ? 1.0f : v1;
+  const int nq4 = io.dp / 4;  // float4s per row
+  if (RV > 0 && nq4 <= 32 * RV) {
+    // Lane l's float4s are l, l + 32, ...: nv of them (the rest of the last step is zero padding).
+    const int nv = (nq4 - lane + 31) / 32;
+    constexpr int R = RV > 0 ? RV : 1;
+    float4 xr[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+      xr[t] = t < nv ? __ldg(reinterpret_cast<const float4*>(xi) + lane + 32 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < K; c += 4) {
+      int j[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) j[u] = w.idx[c + u < K ? c + u : c];
+      float v[4];
+      dot4_reg<R>(xr, nv, io.xhat + size_t(j[0]) * io.dp, io.xhat + size_t(j[1]) * io.dp,
+               io.xhat + size_t(j[2]) * io.dp, io.xhat + size_t(j[3]) * io.dp, lane, v);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (c + u < K) w.s[c + u] = j[u] == i ? 1.0f : v[u];
+      }
+    }
+  } else {
+    for (int c = 0; c < K; c += 2) {
+      const int j0 = w.idx[c];
+      const int j1 = c + 1 < K ? w.idx[c + 1] : j0;
+      float v0, v1;
+      dot2_fp32(xi, io.xhat + size_t(j0) * io.dp, io.xhat + size_t(j1) * io.dp, io.dp, lane, v0, v1);
+      if (lane == 0) {
+        w.s[c] = j0 == i ? 1.0f : v0;
+        if (c + 1 < K) w.s[c + 1] = j1 == i ? 1.0f : v1;
+      }
     }
   }
   for (int c = lane; c < K; c += kWarp) w.need[c] = 0;
@@ -232,6 +287,7 @@ __device__ bool refine_warp(WarpSmem& w, int K, int64_t i, int k1, float B, doub
   return ok;
 }
 
+template <int RV>
 __global__ void __launch_bounds__(WPB * kWarp)
 k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* __restrict__ part_i, int P,
           int K, int k1, ErrModel em, double eps_r, const int32_t* __restrict__ rows,
@@ -264,7 +320,7 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
     if (lane == 0) set_error(io.status, kErrInternal);
     return;
   }
-  const bool ok = refine_warp(w, cnt, i, k1, B, eps_g, eps_r, io, false, lane);
+  const bool ok = refine_warp<RV>(w, cnt, i, k1, B, eps_g, eps_r, io, false, lane);
   if (!ok && lane == 0) {
     const int slot = atomicAdd(fb_count, 1);
     fb_rows[slot] = int32_t(i);
@@ -325,7 +381,7 @@ k2_fallback(RowIo io, int64_t n, int K, int k1, double eps_r, const int32_t* fb_
       const int cnt = merge_lists(w, scratch_s + size_t(blockIdx.x) * FB_WARPS * K,
                                   scratch_i + size_t(blockIdx.x) * FB_WARPS * K, FB_WARPS, K, lane, B);
       if (cnt == n) B = -FLT_MAX;
-      if (cnt >= k1) refine_warp(w, cnt, i, k1, B, eps_r, eps_r, io, true, lane);
+      if (cnt >= k1) refine_warp<0>(w, cnt, i, k1, B, eps_r, eps_r, io, true, lane);
       else if (lane == 0) set_error(io.status, kErrInternal);
     }
     __syncthreads();
@@ -363,8 +419,13 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
   const unsigned blocks = unsigned((g + WPB - 1) / WPB);
   // First pass: uncertified rows go to the recheck; a recheck's failures go to the exact scan.
   const int stat = (rows && !part_by_row) ? kStFallback2 : kStFallback;
-  k2_refine<<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em, rescore_eps(sh.dp), rows,
-                                           count, part_by_row, fb_rows, fb_count, stat);
+  // Row i in registers: 4 float4s per lane up to dp = 512, 16 up to 2048.
+  if (sh.dp <= 512)
+    k2_refine<4><<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em, rescore_eps(sh.dp),
+                                                rows, count, part_by_row, fb_rows, fb_count, stat);
+  else
+    k2_refine<16><<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em, rescore_eps(sh.dp),
+                                                 rows, count, part_by_row, fb_rows, fb_count, stat);
   return 1;
 }
 
