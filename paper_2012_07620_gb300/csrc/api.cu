@@ -8,6 +8,8 @@
 #include <new>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -202,7 +204,14 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
   const Shape& sh = j.sh;
   const Buffers& b = j.b;
   long long* status = j.st;
+  // NVTX: one range per instance on the host timeline, a marker per stage
+  // (no-ops unless a profiler is attached).
+  nvtxRangePushA("rerank instance");
+  struct PopRange {
+    ~PopRange() { nvtxRangePop(); }
+  } pop_range;
   auto mark = [&](const char* name) {
+    nvtxMarkA(name);
     if (tm) tm->mark(name);
   };
   int64_t nl = 1;

@@ -32,6 +32,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -322,6 +324,10 @@ void CUDART_CB on_done(void* p) {
 
 // Enqueue one request on its slot.  No host synchronisation.
 rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cudaEvent_t ready) {
+  nvtxRangePushA("rerank request");
+  struct PopRange {
+    ~PopRange() { nvtxRangePop(); }
+  } pop_range;
   rerank_ctx* ctx = v.ctx;
   const int64_t Q = rq.nq, G = v.G, n = G + Q, base = v.S - Q;
   const int64_t topk = rq.topk_out ? rq.topk_out : G;
