@@ -200,7 +200,19 @@ void finish_timing(rerank_ctx* ctx) {
 }
 
 // Enqueue every stage of one instance on `s` (no host synchronisation).
-rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches) {
+cudaError_t ensure_copy_stream(rerank_ctx* ctx) {
+  if (ctx->copy_stream) return cudaSuccess;
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking);
+  for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) ctx->copy_events.push_back(ev);
+  }
+  return e;
+}
+
+rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches,
+                          bool copy_overlap) {
   const Shape& sh = j.sh;
   const Buffers& b = j.b;
   long long* status = j.st;
@@ -316,14 +328,35 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     nl += launch_row_norms(sh, b, src, status, s);
     int32_t* oi = sh.host_out ? b.out_idx : j.out_idx;
     float* od = sh.host_out ? b.out_dist : j.out_dist;
-    nl += launch_rank(sh, b, src, oi, od, status, ctx->sm_count, sh.tune, s);
-    RR_CUDA(cudaGetLastError());
-    mark("rank");
-    if (sh.host_out) {
-      const size_t cnt = size_t(sh.nq) * sh.topk;
-      RR_CUDA(cudaMemcpyAsync(j.out_idx, b.out_idx, cnt * 4, cudaMemcpyDeviceToHost, s));
-      RR_CUDA(cudaMemcpyAsync(j.out_dist, b.out_dist, cnt * 4, cudaMemcpyDeviceToHost, s));
-      mark("d2h");
+    if (sh.host_out && copy_overlap && sh.nq >= 4 * int64_t(ctx->sm_count)) {
+      // Host outputs: rank the queries in four parts and copy each part back on
+      // a second stream while the next part is ranked.
+      RR_CUDA(ensure_copy_stream(ctx));
+      nl += launch_rank_prep(sh, b, src, status, s);
+      const int parts = 4;
+      for (int p = 0; p < parts; ++p) {
+        const int64_t q0 = sh.nq * p / parts, q1 = sh.nq * (p + 1) / parts;
+        nl += launch_rank_queries(sh, b, src, oi, od, q0, q1, status, ctx->sm_count, sh.tune, s);
+        RR_CUDA(cudaEventRecord(ctx->copy_events[size_t(p)], s));
+        RR_CUDA(cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_events[size_t(p)], 0));
+        const size_t off = size_t(q0) * size_t(sh.topk), cnt = size_t(q1 - q0) * size_t(sh.topk);
+        RR_CUDA(cudaMemcpyAsync(j.out_idx + off, oi + off, cnt * 4, cudaMemcpyDeviceToHost, ctx->copy_stream));
+        RR_CUDA(cudaMemcpyAsync(j.out_dist + off, od + off, cnt * 4, cudaMemcpyDeviceToHost, ctx->copy_stream));
+      }
+      RR_CUDA(cudaEventRecord(ctx->copy_events[size_t(parts)], ctx->copy_stream));
+      RR_CUDA(cudaStreamWaitEvent(s, ctx->copy_events[size_t(parts)], 0));
+      RR_CUDA(cudaGetLastError());
+      mark("rank_d2h");
+    } else {
+      nl += launch_rank(sh, b, src, oi, od, status, ctx->sm_count, sh.tune, s);
+      RR_CUDA(cudaGetLastError());
+      mark("rank");
+      if (sh.host_out) {
+        const size_t cnt = size_t(sh.nq) * sh.topk;
+        RR_CUDA(cudaMemcpyAsync(j.out_idx, b.out_idx, cnt * 4, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaMemcpyAsync(j.out_dist, b.out_dist, cnt * 4, cudaMemcpyDeviceToHost, s));
+        mark("d2h");
+      }
     }
   }
   *launches += nl;
@@ -374,7 +407,7 @@ rerank_status run_once(rerank_ctx* ctx, const void* xq, const void* xg, int32_t*
   tm.stream = s;
   tm.mark("begin");
   int64_t nl = 0;
-  st = enqueue_job(ctx, j, s, &tm, &nl);
+  st = enqueue_job(ctx, j, s, &tm, &nl, true);
   if (st != RERANK_OK) return st;
   ctx->launches = nl;
   RR_CUDA(cudaGetLastError());
@@ -684,6 +717,8 @@ rerank_status rerank_destroy(rerank_ctx* ctx) {
   for (auto e : ctx->timer.ev) cudaEventDestroy(e);
   for (auto st : ctx->streams) cudaStreamDestroy(st);
   for (auto e : ctx->events) cudaEventDestroy(e);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (auto e : ctx->copy_events) cudaEventDestroy(e);
   if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
   delete ctx;
   return RERANK_OK;

@@ -176,6 +176,9 @@ struct rerank_ctx {
   // and a pinned copy of every instance's status block
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;   // [0] fork, [1 + i] join of streams[i]
+  // single calls with host outputs: results copied back while later queries are ranked
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> copy_events;
   long long* h_batch = nullptr;
   size_t h_batch_count = 0;
   rr::ServeHandle* serve = nullptr;
@@ -249,6 +252,11 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
 int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s);
 int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist,
                  long long* status, int sm_count, const Tuning& t, cudaStream_t s);
+// The same in two parts: the gallery's column lists once, then queries [q0, q1)
+// (out_idx / out_dist still address the whole nq x topk output).
+int launch_rank_prep(const Shape& sh, const Buffers& b, int src, long long* status, cudaStream_t s);
+int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist, int64_t q0,
+                        int64_t q1, long long* status, int sm_count, const Tuning& t, cudaStream_t s);
 
 size_t rank_smem_bytes(int64_t ng, int threads);
 
@@ -270,7 +278,10 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
 rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, int dtype, int k1, int k2,
                          int layers, int64_t topk, bool knn_only, bool host_in, bool host_out, int64_t cap_hint,
                          Shape* out, const Tuning* tune = nullptr);  // tune: override of the table lookup
-rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches);
+// copy_overlap: host outputs are copied back in parts while later queries are
+// ranked (single calls only; batched instances copy on their own stream).
+rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches,
+                          bool copy_overlap = false);
 rerank_status map_status(const long long* h, int precision, rerank_info* info, int64_t* need);
 int launch_status_reset(long long* st, cudaStream_t s);
 // Tuning of an instance: the table entry for (precision, d, bucket of n), else defaults.

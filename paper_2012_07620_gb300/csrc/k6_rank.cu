@@ -156,6 +156,7 @@ struct RankArgs {
   const int32_t* csc_row;
   const float* csc_val;
   int64_t nq, ng, topk;
+  int64_t q_begin, q_end;  // queries ranked by this launch
   int32_t* out_idx;
   float* out_dist;
   uint32_t* gscratch;   // per CTA: acc (ng) [if !acc_smem] + 4 * ng sort buffers
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
   uint32_t* gv1 = gk1 + ng;
   const int64_t T = A.topk;
 
-  for (int64_t q = blockIdx.x; q < A.nq; q += gridDim.x) {
+  for (int64_t q = A.q_begin + blockIdx.x; q < A.q_end; q += gridDim.x) {
     for (int64_t g = t; g < ng; g += RT) acc[g] = 0u;
     __syncthreads();
     const int64_t a = A.start[q];
@@ -300,7 +301,12 @@ size_t rank_smem_bytes(int64_t ng, int threads) {
 
 int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist, long long* status,
                  int sm_count, const Tuning& tune, cudaStream_t s) {
-  (void)tune;
+  int nl = launch_rank_prep(sh, b, src, status, s);
+  nl += launch_rank_queries(sh, b, src, out_idx, out_dist, 0, sh.nq, status, sm_count, tune, s);
+  return nl;
+}
+
+int launch_rank_prep(const Shape& sh, const Buffers& b, int src, long long* status, cudaStream_t s) {
   const int64_t n = sh.n, nq = sh.nq, ng = sh.ng;
   const int T = 256;
   cudaMemsetAsync(b.colcnt, 0, sizeof(int32_t) * (n + 1), s);
@@ -310,6 +316,14 @@ int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, fl
   cudaMemsetAsync(b.colcnt, 0, sizeof(int32_t) * (n + 1), s);
   k5_fill<<<unsigned((ng * kWarp + T - 1) / T), T, 0, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.rnorm,
                                                            nq, n, b.colptr, b.colcnt, b.csc_row, b.csc_val, status);
+  return 3;
+}
+
+int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist, int64_t q0,
+                        int64_t q1, long long* status, int sm_count, const Tuning& tune, cudaStream_t s) {
+  (void)tune;
+  (void)sm_count;
+  const int64_t nq = sh.nq, ng = sh.ng;
   RankArgs A;
   A.start = b.start[src];
   A.len = b.len[src];
@@ -322,6 +336,8 @@ int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, fl
   A.nq = nq;
   A.ng = ng;
   A.topk = sh.topk;
+  A.q_begin = q0;
+  A.q_end = q1;
   A.out_idx = out_idx;
   A.out_dist = out_dist;
   A.gscratch = b.rank_scratch;
@@ -329,8 +345,10 @@ int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, fl
   A.acc_smem = smem > rank_smem_fixed(ng);
   A.status = status;
   cudaFuncSetAttribute(k6_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  k6_rank<<<sh.rank_ctas, RT, smem, s>>>(A);
-  return 4;
+  const int64_t nqry = q1 - q0;
+  const unsigned grid = unsigned(nqry < sh.rank_ctas ? (nqry > 0 ? nqry : 1) : sh.rank_ctas);
+  k6_rank<<<grid, RT, smem, s>>>(A);
+  return 1;
 }
 
 int rank_threads() { return RT; }

@@ -123,6 +123,17 @@ def test_host_buffers_match_device(R):
     assert (hi == di).all() and (hd == dd).all()
 
 
+@pytest.mark.parametrize("topk", [0, 37])
+def test_host_outputs_copied_in_parts_match_device(R, topk):
+    """With host outputs and enough queries the call ranks the queries in parts
+    and copies each part back while the next is ranked: same bits as device outputs."""
+    spec = synthetic.WorkloadSpec("many_queries", 1300, 2100, 96, 160, 0.35, 0, None, seed=12)
+    w = synthetic.make_workload(spec)
+    di, dd = _gpu(R, w.xq, w.xg, 20, 5, 2, topk)
+    hi, hd = R.run(w.xq, w.xg, 20, 5, 2, topk)
+    assert (hi == di).all() and (hd == dd).all()
+
+
 def test_repeat_is_bitwise_identical(R):
     w = synthetic.make_workload(synthetic.TINY)
     a = _gpu(R, w.xq, w.xg, 26, 7, 2)
