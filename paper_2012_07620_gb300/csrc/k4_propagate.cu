@@ -121,22 +121,82 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
     const int m = nbr_n[i];
     int distinct = 0;
     bool spilled = false;
-    for (int q = 0; q < m && !spilled; ++q) {
-      const int32_t j = nbr[i * k2p1 + q];
-      const float cj = nbr_w[i * k2p1 + q];
-      const int64_t a = sstart[j];
-      const int lj = slen[j];
-      for (int e0 = 0; e0 < lj; e0 += kWarp) {
-        const int e = e0 + lane;
-        bool fresh = false;
-        if (e < lj) fresh = hash_add(keys, vals, mask, shift, scol[a + e], cj * sval[a + e], status);
-        distinct += __popc(__ballot_sync(kFull, fresh));
-        __syncwarp();  // this step's table writes are visible to the next step
-        if (distinct > limit) {
-          spilled = true;
-          break;
+    // Lane q < m holds message q's source row (start, length) and weight; the
+    // messages are folded in order, 32 entries per step, and the entries of
+    // the next step are loaded while this step is added to the table.
+    int64_t qa = 0;
+    int ql = 0;
+    float qc = 0.f;
+    if (m > kWarp) {
+      // more messages than lanes (k2 >= 32): one message at a time
+      for (int q = 0; q < m && !spilled; ++q) {
+        const int32_t j = nbr[i * k2p1 + q];
+        const float cj = nbr_w[i * k2p1 + q];
+        const int64_t a = sstart[j];
+        const int lj = slen[j];
+        for (int e0 = 0; e0 < lj; e0 += kWarp) {
+          const int e = e0 + lane;
+          bool fresh = false;
+          if (e < lj) fresh = hash_add(keys, vals, mask, shift, scol[a + e], cj * sval[a + e], status);
+          distinct += __popc(__ballot_sync(kFull, fresh));
+          __syncwarp();
+          if (distinct > limit) {
+            spilled = true;
+            break;
+          }
         }
       }
+    }
+    const int mq = m > kWarp ? 0 : m;  // messages handled by the pipelined loop
+    if (lane < mq) {
+      const int32_t j = nbr[i * k2p1 + lane];
+      qc = nbr_w[i * k2p1 + lane];
+      qa = sstart[j];
+      ql = slen[j];
+    }
+    int q = 0, e0 = 0;
+    while (q < mq && __shfl_sync(kFull, ql, q) == 0) ++q;
+    int col = -1;
+    float val = 0.f;
+    if (q < mq) {
+      const int64_t a = __shfl_sync(kFull, qa, q);
+      const int lj = __shfl_sync(kFull, ql, q);
+      if (lane < lj) {
+        col = scol[a + lane];
+        val = sval[a + lane];
+      }
+    }
+    while (q < mq) {
+      // next step: (q, e0 + 32) or the next non-empty message
+      int nq = q, ne0 = e0 + kWarp;
+      if (ne0 >= __shfl_sync(kFull, ql, q)) {
+        ne0 = 0;
+        ++nq;
+        while (nq < mq && __shfl_sync(kFull, ql, nq) == 0) ++nq;
+      }
+      int ncol = -1;
+      float nval = 0.f;
+      if (nq < mq) {
+        const int64_t a = __shfl_sync(kFull, qa, nq);
+        const int lj = __shfl_sync(kFull, ql, nq);
+        if (ne0 + lane < lj) {
+          ncol = scol[a + ne0 + lane];
+          nval = sval[a + ne0 + lane];
+        }
+      }
+      const float cj = __shfl_sync(kFull, qc, q);
+      bool fresh = false;
+      if (col >= 0) fresh = hash_add(keys, vals, mask, shift, col, cj * val, status);
+      distinct += __popc(__ballot_sync(kFull, fresh));
+      __syncwarp();  // this step's table writes are visible to the next step
+      if (distinct > limit) {
+        spilled = true;
+        break;
+      }
+      q = nq;
+      e0 = ne0;
+      col = ncol;
+      val = nval;
     }
     if (spilled) {
       for (int s = lane; s < T; s += kWarp) {
