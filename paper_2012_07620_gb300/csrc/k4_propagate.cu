@@ -5,9 +5,10 @@
 //
 // where M(i) is the message list built by K3 (N(i, k2) with c_j = e_ij^alpha,
 // the residual h_i folded into c_i).  Features are stored as padded CSR: row
-// i occupies [start_i, start_i + len_i) of (col, val) with columns ascending.
-// start_i is an exclusive scan of ub_i = sum_j len_j, an upper bound on the
-// output row, so every row can be written without a second pass.
+// i occupies [start_i, start_i + len_i) of (col, val), each column at most
+// once, in no particular order (h^(0) from K3 is ascending).  start_i is an
+// exclusive scan of ub_i = sum_j len_j, an upper bound on the output row, so
+// every row can be written without a second pass.
 //
 // Rows whose distinct columns fit three quarters of a 1024-slot table (almost
 // all): one warp per row with a private open-addressing hash table in shared
@@ -15,7 +16,10 @@
 // walks the message list in order and adds c_j * val into the table, one
 // list at a time, so every output value is summed in message-list order and
 // the result does not depend on scheduling.  The occupied slots are
-// compacted, sorted by column (bitonic), scaled by 1/||row|| and written.
+// compacted in table order, scaled by 1/||row|| and written: a column's
+// position in the row never matters (a later layer folds each column's terms
+// in message order wherever they sit, and the norm is summed exactly as
+// 128-bit fixed point, so it does not depend on the order either).
 // Larger rows: one CTA per row with a dense accumulator and a bitmap of
 // touched columns in global memory; the bitmap scan emits columns in order.
 #include "common.cuh"
@@ -81,6 +85,29 @@ __device__ __forceinline__ bool hash_add(volatile int* keys, float* vals, int ma
   }
   set_error(status, kErrInternal);
   return false;
+}
+
+// Sum of squares of v[0 .. cnt) by one warp, independent of the order of the
+// values: each square is exact in double, is truncated to a multiple of
+// 2^-64, and the truncated squares are added as 128-bit integers.
+__device__ float warp_sumsq_exact(const float* v, int cnt, int lane) {
+  unsigned long long hi = 0, lo = 0;
+  for (int p = lane; p < cnt; p += kWarp) {
+    const double d = double(v[p]) * double(v[p]);
+    const double ip = floor(d);
+    const unsigned long long h = static_cast<unsigned long long>(ip);
+    const unsigned long long l = static_cast<unsigned long long>((d - ip) * 18446744073709551616.0);  // x 2^64
+    lo += l;
+    hi += h + (lo < l ? 1ull : 0ull);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long oh = __shfl_xor_sync(kFull, hi, o), ol = __shfl_xor_sync(kFull, lo, o);
+    const unsigned long long nl = lo + ol;
+    hi = hi + oh + (nl < lo ? 1ull : 0ull);
+    lo = nl;
+  }
+  return float(double(hi) + double(lo) * 5.421010862427522e-20);  // 2^-64
 }
 
 __device__ __forceinline__ int next_pow2(int x) {
@@ -223,30 +250,11 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
       cnt += __popc(bal);
       __syncwarp();
     }
-    const int P2 = next_pow2(max(cnt, 2));
-    for (int s = cnt + lane; s < P2; s += kWarp) keys[s] = kInvalidIdx;
-    __syncwarp();
-    // Bitonic sort of (key, val) by key over P2 slots.
-    for (int k = 2; k <= P2; k <<= 1) {
-      for (int jj = k >> 1; jj > 0; jj >>= 1) {
-        for (int t = lane; t < P2 / 2; t += kWarp) {
-          const int i1 = (t / jj) * 2 * jj + (t % jj), i2 = i1 + jj;
-          const bool up = (i1 & k) == 0;
-          const int ka = keys[i1], kb = keys[i2];
-          if ((ka > kb) == up) {
-            keys[i1] = kb;
-            keys[i2] = ka;
-            const float va = vals[i1];
-            vals[i1] = vals[i2];
-            vals[i2] = va;
-          }
-        }
-        __syncwarp();
-      }
-    }
-    float ss = 0.f;
-    for (int p = lane; p < cnt; p += kWarp) ss = fmaf(vals[p], vals[p], ss);
-    ss = warp_sum(ss);
+    // The row is written in table order: its columns' order never matters
+    // downstream (each column occurs once per row, so a later layer folds a
+    // column's terms in message order whatever the positions), and the norm
+    // below is independent of the order.
+    const float ss = warp_sumsq_exact(vals, cnt, lane);
     const float inv = 1.0f / sqrtf(ss);
     const int64_t o = dstart[i];
     for (int p = lane; p < cnt; p += kWarp) {
@@ -346,9 +354,7 @@ __global__ void k4_row_norms(const int64_t* __restrict__ start, const int32_t* _
   if (i >= n || (status[kStErr] & kErrOverflow)) return;
   const int64_t a = start[i];
   const int m = len[i];
-  float ss = 0.f;
-  for (int p = lane; p < m; p += kWarp) ss = fmaf(val[a + p], val[a + p], ss);
-  ss = warp_sum(ss);
+  const float ss = warp_sumsq_exact(val + a, m, lane);
   if (lane == 0) rn[i] = 1.0f / sqrtf(ss);
 }
 

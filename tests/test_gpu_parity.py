@@ -55,7 +55,8 @@ def _check_all(R, xq, xg, k1, k2, layers, topk=0, check_h=True):
         a = ref.a_star.tocsr()
         a.sort_indices()
         assert (rp == a.indptr).all() and (col == a.indices).all() and (val == a.data).all()
-        # h^(L): same supports, values within FP32 accuracy
+        # h^(L): same supports, values within FP32 accuracy (layer rows are
+        # stored in no particular column order: compare them sorted)
         st = R.debug("hl_start")[:n]
         ln = R.debug("hl_len")[:n]
         hc = R.debug("hl_col")
@@ -65,6 +66,8 @@ def _check_all(R, xq, xg, k1, k2, layers, topk=0, check_h=True):
         for i in range(0, n, max(1, n // 97)):
             c = hc[st[i]: st[i] + ln[i]]
             v = hv[st[i]: st[i] + ln[i]]
+            order = np.argsort(c, kind="stable")
+            c, v = c[order], v[order]
             rc = hl.indices[hl.indptr[i]: hl.indptr[i + 1]]
             rv = hl.data[hl.indptr[i]: hl.indptr[i + 1]]
             assert (c == rc).all(), i
