@@ -54,6 +54,9 @@ struct RowIo {
   long long* status;
 };
 
+__device__ __forceinline__ float to_float(float x) { return x; }
+__device__ __forceinline__ float to_float(__nv_bfloat16 x) { return __bfloat162float(x); }
+
 __device__ __forceinline__ const void* raw_row(const RowIo& io, int64_t r, size_t& base) {
   if (r < io.nq) {
     base = size_t(r) * io.d;
@@ -63,13 +66,35 @@ __device__ __forceinline__ const void* raw_row(const RowIo& io, int64_t r, size_
   return io.xg;
 }
 
+// Lane l's FMA chain over elements l, l + 32, ... in that order; the loads of
+// eight steps are issued before their FMAs.
+template <class T>
+__device__ __forceinline__ double dot_fp64_chain(const T* fa, const T* fb, int d, int lane) {
+  double acc = 0.0;
+  int k = lane;
+  for (; k + 7 * kWarp < d; k += 8 * kWarp) {
+    float x[8], y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      x[u] = to_float(fa[k + u * kWarp]);
+      y[u] = to_float(fb[k + u * kWarp]);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc = fma(double(x[u]), double(y[u]), acc);
+  }
+  for (; k < d; k += kWarp) acc = fma(double(to_float(fa[k])), double(to_float(fb[k])), acc);
+  return acc;
+}
+
 __device__ double dot_fp64_raw(const RowIo& io, int64_t a, int64_t b, int lane) {
   size_t ba, bb;
   const void* pa = raw_row(io, a, ba);
   const void* pb = raw_row(io, b, bb);
-  double acc = 0.0;
-  for (int k = lane; k < io.d; k += kWarp)
-    acc = fma(double(load_feat(pa, io.dtype, ba + k)), double(load_feat(pb, io.dtype, bb + k)), acc);
+  const double acc =
+      io.dtype == 0
+          ? dot_fp64_chain(static_cast<const float*>(pa) + ba, static_cast<const float*>(pb) + bb, io.d, lane)
+          : dot_fp64_chain(static_cast<const __nv_bfloat16*>(pa) + ba, static_cast<const __nv_bfloat16*>(pb) + bb,
+                           io.d, lane);
   return warp_sum(acc);
 }
 
@@ -177,56 +202,81 @@ __device__ __forceinline__ void dot4_reg(const float4 (&xr)[RV], int nv, const f
 // RV > 0: keep row i in registers when dp <= 128 RV (the warp-per-row
 // kernel; the fallback's 1024-thread CTAs have no registers to spare).
 template <int RV>
-__device__ bool refine_warp(WarpSmem& w, int K, int64_t i, int k1, float B, double eps_g, double eps_r,
+__device__ bool refine_warp(WarpSmem& w, int Kc, int64_t i, int k1, float B, double eps_g, double eps_r,
                             const RowIo& io, bool last, int lane) {
   const float* xi = io.xhat + size_t(i) * io.dp;
   const int nq4 = io.dp / 4;  // float4s per row
-  if (RV > 0 && nq4 <= 32 * RV) {
-    // Lane l's float4s are l, l + 32, ...: nv of them (the rest of the last step is zero padding).
-    const int nv = (nq4 - lane + 31) / 32;
-    constexpr int R = RV > 0 ? RV : 1;
-    float4 xr[R];
+  const bool reg = RV > 0 && nq4 <= 32 * RV;
+  // Lane l's float4s are l, l + 32, ...: nv of them (the rest of the last step is zero padding).
+  const int nv = (nq4 - lane + 31) / 32;
+  constexpr int R = RV > 0 ? RV : 1;
+  float4 xr[R];
+  if (reg) {
 #pragma unroll
     for (int t = 0; t < R; ++t)
       xr[t] = t < nv ? __ldg(reinterpret_cast<const float4*>(xi) + lane + 32 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int c = 0; c < K; c += 4) {
-      int j[4];
+  }
+  // FP32 scores of candidates [c0, c1) into w.s.
+  auto rescore = [&](int c0, int c1) {
+    if (reg) {
+      for (int c = c0; c < c1; c += 4) {
+        int j[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) j[u] = w.idx[c + u < K ? c + u : c];
-      float v[4];
-      dot4_reg<R>(xr, nv, io.xhat + size_t(j[0]) * io.dp, io.xhat + size_t(j[1]) * io.dp,
-               io.xhat + size_t(j[2]) * io.dp, io.xhat + size_t(j[3]) * io.dp, lane, v);
-      if (lane == 0) {
+        for (int u = 0; u < 4; ++u) j[u] = w.idx[c + u < c1 ? c + u : c];
+        float v[4];
+        dot4_reg<R>(xr, nv, io.xhat + size_t(j[0]) * io.dp, io.xhat + size_t(j[1]) * io.dp,
+                    io.xhat + size_t(j[2]) * io.dp, io.xhat + size_t(j[3]) * io.dp, lane, v);
+        if (lane == 0) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (c + u < K) w.s[c + u] = j[u] == i ? 1.0f : v[u];
+          for (int u = 0; u < 4; ++u)
+            if (c + u < c1) w.s[c + u] = j[u] == i ? 1.0f : v[u];
+        }
+      }
+    } else {
+      for (int c = c0; c < c1; c += 2) {
+        const int j0 = w.idx[c];
+        const int j1 = c + 1 < c1 ? w.idx[c + 1] : j0;
+        float v0, v1;
+        dot2_fp32(xi, io.xhat + size_t(j0) * io.dp, io.xhat + size_t(j1) * io.dp, io.dp, lane, v0, v1);
+        if (lane == 0) {
+          w.s[c] = j0 == i ? 1.0f : v0;
+          if (c + 1 < c1) w.s[c + 1] = j1 == i ? 1.0f : v1;
+        }
       }
     }
-  } else {
-    for (int c = 0; c < K; c += 2) {
-      const int j0 = w.idx[c];
-      const int j1 = c + 1 < K ? w.idx[c + 1] : j0;
-      float v0, v1;
-      dot2_fp32(xi, io.xhat + size_t(j0) * io.dp, io.xhat + size_t(j1) * io.dp, io.dp, lane, v0, v1);
-      if (lane == 0) {
-        w.s[c] = j0 == i ? 1.0f : v0;
-        if (c + 1 < K) w.s[c + 1] = j1 == i ? 1.0f : v1;
-      }
+    __syncwarp();
+  };
+  // Rank of each rescored candidate among [0, n): w.ord[rank] = candidate.
+  auto rank_all = [&](int n) {
+    for (int c = lane; c < n; c += kWarp) {
+      const float sc = w.s[c];
+      const int ic = w.idx[c];
+      int r = 0;
+      for (int e = 0; e < n; ++e) r += ranks_before(w.s[e], w.idx[e], sc, ic) ? 1 : 0;
+      w.ord[r] = c;
     }
+    __syncwarp();
+  };
+  // Lazy rescoring: the candidates come sorted by approximate score; rescore
+  // the first k1 + 4, then 8 more at a time, until the best approximate score
+  // left (plus its bound) stays 3 eps_r below the k1-th rescored score.  The
+  // rest cannot then reach the top-k1, nor a near-tie run inside it, so the
+  // result is that of rescoring all Kc candidates.
+  int K = tmin(Kc, (k1 + 7) & ~3);
+  rescore(0, K);
+  rank_all(K);
+  while (K < Kc && !(double(w.s[w.ord[k1 - 1]]) - 3.0 * eps_r > double(w.g[K]) + eps_g)) {
+    const int K2 = tmin(Kc, K + 8);
+    rescore(K, K2);
+    K = K2;
+    rank_all(K);
   }
   for (int c = lane; c < K; c += kWarp) w.need[c] = 0;
   __syncwarp();
-  for (int c = lane; c < K; c += kWarp) {
-    const float sc = w.s[c];
-    const int ic = w.idx[c];
-    int r = 0;
-    for (int e = 0; e < K; ++e) r += ranks_before(w.s[e], w.idx[e], sc, ic) ? 1 : 0;
-    w.ord[r] = c;
-  }
-  __syncwarp();
 
+  // Certificate: every column outside the candidates scores at most B (approximately).
   bool ok = true;
-  if (B > -FLT_MAX) ok = double(w.s[w.ord[k1 - 1]]) - eps_r > double(B) + eps_g;
+  if (K == Kc && B > -FLT_MAX) ok = double(w.s[w.ord[k1 - 1]]) - eps_r > double(B) + eps_g;
   if (!ok && !last) return false;
 
   // Runs of near-equal FP32 scores that reach into the top-k1.
