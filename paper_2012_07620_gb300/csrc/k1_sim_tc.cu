@@ -31,6 +31,8 @@
 #include <cfloat>
 #include <climits>
 
+#include <cstdlib>
+
 #include "common.cuh"
 #include "internal.hpp"
 #include "tc_ptx.cuh"
@@ -79,6 +81,7 @@ struct TcArgs {
   const int32_t* rows;      // split mode: global row of each A row
   const int32_t* count;     // split mode: number of A rows
   int* row_floor;           // per A row: score_key of the best K-th score any finished chunk found
+  int stall;                // test hook: the TMA warp issues nothing, so every wait runs out
   float* part_s;
   int32_t* part_i;
   long long* status;
@@ -142,7 +145,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       uint32_t armed = 0;  // bit s: slot s holds a load that may still be in flight
       uint32_t armed_phase = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      for (int item = blockIdx.x; item < items && ok && !A.stall; item += gridDim.x) {
         int rb, chunk, t0, t1;
         item_range(A, row_blocks, item, rb, chunk, t0, t1);
         for (int ct = t0; ct < t1 && ok; ++ct) {
@@ -352,6 +355,11 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
   if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
+// Test hook: RERANK_TEST_TC_STALL set in the environment makes the kernels'
+// TMA warp issue nothing, so the MMA and epilogue waits run out and the call
+// returns ETIMEOUT (no copy or MMA is ever in flight on that path).
+int stall_hook() { return std::getenv("RERANK_TEST_TC_STALL") ? 1 : 0; }
+
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -450,6 +458,7 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   A.part_s = part_s;
   A.part_i = part_i;
   A.status = status;
+  A.stall = stall_hook();
   const int items = A.row_blocks * A.chunks;
   const int grid = items < sm_count ? items : sm_count;
   if (fp8)
@@ -486,6 +495,7 @@ int launch_sim_tc_rect_topk(const Shape& sh, const void* a, int64_t a_rows, int6
   A.part_s = part_s;
   A.part_i = part_i;
   A.status = status;
+  A.stall = stall_hook();
   const int items = A.row_blocks * A.chunks;
   const int grid = items < sm_count ? items : sm_count;
   if (fp8)
@@ -519,6 +529,7 @@ int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, 
   A.part_s = part_s;
   A.part_i = part_i;
   A.status = status;
+  A.stall = stall_hook();
   launch_mode<MODE_SPLIT>(a0, a1, b0, b1, A, eg, sm_count, s);
   return 1;
 }

@@ -119,14 +119,18 @@ __device__ __forceinline__ void dot2_fp32(const float* xi, const float* y0, cons
 
 // P-way merge of sorted candidate lists src[p*K .. p*K+K) for p < P (P <= 32),
 // one list per lane.  Fills w.idx/w.g with the best K; returns the count and
-// the bound B on every candidate that was not taken.
-__device__ int merge_lists(WarpSmem& w, const float* ls, const int32_t* li, int P, int K, int lane, float& B) {
+// the bound B on every candidate that was not taken.  An index outside
+// [0, n) ends its list (lists left unwritten by an aborted similarity stage
+// must not send the refinement outside the feature rows).
+__device__ int merge_lists(WarpSmem& w, const float* ls, const int32_t* li, int P, int K, int64_t n, int lane,
+                           float& B) {
   int head = 0;
   float hs = -FLT_MAX;
   int hi = kInvalidIdx;
   if (lane < P) {
     hs = ls[lane * K];
     hi = li[lane * K];
+    if (hi < 0 || hi >= n) hi = kInvalidIdx;
   }
   int cnt = 0;
   for (; cnt < K; ++cnt) {
@@ -153,6 +157,7 @@ __device__ int merge_lists(WarpSmem& w, const float* ls, const int32_t* li, int 
       if (head < K) {
         hs = ls[lane * K + head];
         hi = li[lane * K + head];
+        if (hi < 0 || hi >= n) hi = kInvalidIdx;
       } else {
         hs = -FLT_MAX;
         hi = kInvalidIdx;
@@ -364,13 +369,11 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
   WarpSmem& w = sm[wib];
   float B;
   const size_t base = size_t(part_by_row ? i : f) * P * K;
-  const int cnt = merge_lists(w, part_s + base, part_i + base, P, K, lane, B);
+  const int cnt = merge_lists(w, part_s + base, part_i + base, P, K, n, lane, B);
   if (cnt == n) B = -FLT_MAX;  // every column is a candidate
-  if (cnt < k1) {
-    if (lane == 0) set_error(io.status, kErrInternal);
-    return;
-  }
-  const bool ok = refine_warp<RV>(w, cnt, i, k1, B, eps_g, eps_r, io, false, lane);
+  // Fewer than k1 candidates (only after an aborted similarity stage): the
+  // row goes to the next, exact stage like an uncertified one.
+  const bool ok = cnt >= k1 && refine_warp<RV>(w, cnt, i, k1, B, eps_g, eps_r, io, false, lane);
   if (!ok && lane == 0) {
     const int slot = atomicAdd(fb_count, 1);
     fb_rows[slot] = int32_t(i);
@@ -429,7 +432,7 @@ k2_fallback(RowIo io, int64_t n, int K, int k1, double eps_r, const int32_t* fb_
     if (warp == 0) {
       float B;
       const int cnt = merge_lists(w, scratch_s + size_t(blockIdx.x) * FB_WARPS * K,
-                                  scratch_i + size_t(blockIdx.x) * FB_WARPS * K, FB_WARPS, K, lane, B);
+                                  scratch_i + size_t(blockIdx.x) * FB_WARPS * K, FB_WARPS, K, n, lane, B);
       if (cnt == n) B = -FLT_MAX;
       if (cnt >= k1) refine_warp<0>(w, cnt, i, k1, B, eps_r, eps_r, io, true, lane);
       else if (lane == 0) set_error(io.status, kErrInternal);

@@ -32,7 +32,7 @@ __global__ void k_top_nb(const float* __restrict__ part_s, const int32_t* __rest
   for (int p = 0; p < P; ++p) {
     for (int e = 0; e < NB + 1 && e < K; ++e) {  // the lists are sorted: the first NB+1 cover self
       const int c = part_i[base + size_t(p) * K + e];
-      if (c == kInvalidIdx || c == i) continue;
+      if (c < 0 || c >= n || c == i) continue;  // empty slot (or a list an aborted stage left unwritten)
       float s = part_s[base + size_t(p) * K + e];
       int ci = c;
 #pragma unroll
