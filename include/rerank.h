@@ -65,7 +65,8 @@ enum { RERANK_FEAT_ASTAR = 0, RERANK_FEAT_A = 1, RERANK_FEAT_X = 2 };
 typedef struct {
   int device;                /* CUDA device ordinal */
   int precision;             /* RERANK_PREC_*; default FP32 */
-  int rescore_m;             /* extra candidates kept per row before exact rescoring; default 16 */
+  int rescore_m;             /* extra candidates kept per row before exact rescoring; default 16
+                                (an autotuner table entry may override it per instance size) */
   float alpha;               /* exponent of Eq. 14; default 2 */
   int aggregator;            /* RERANK_AGG_*; default SUM (Sec. 4.1) */
   int feature_mode;          /* RERANK_FEAT_*; default ASTAR */
@@ -294,7 +295,7 @@ rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int dtype, int
 /* Counters of the last rerank_run / rerank_knn call on this context. */
 typedef struct {
   int64_t n_vertices;
-  int64_t candidates_per_row;  /* K = min(k1 + rescore_m, n) */
+  int64_t candidates_per_row;  /* K = min(k1 + m, n), m = rescore_m or the tuned margin */
   int64_t fp64_rescored;       /* candidate scores recomputed in FP64 near a tie */
   int64_t fallback_rows;       /* rows whose first candidate list could not be certified */
   int64_t exact_scan_rows;     /* rows finally redone by the exact FP32 scan of all columns */
@@ -324,7 +325,7 @@ enum {
   RERANK_DBG_H0_VAL = 4,     /* nnz float */
   RERANK_DBG_HL_START = 5,   /* n int64: row start of h^(L) in the padded CSR */
   RERANK_DBG_HL_LEN = 6,     /* n int32: row length of h^(L) */
-  RERANK_DBG_HL_COL = 7,     /* capacity int32 (read rows through START/LEN) */
+  RERANK_DBG_HL_COL = 7,     /* capacity int32 (read rows through START/LEN; columns in no set order) */
   RERANK_DBG_HL_VAL = 8,     /* capacity float */
   RERANK_DBG_PART_S = 9,     /* n x P x K float: per-chunk candidate scores of the similarity kernel */
   RERANK_DBG_PART_I = 10,    /* n x P x K int32: their column indices (0x7fffffff = empty slot) */
