@@ -192,13 +192,47 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     const int64_t a = A.start[q];
     const int m = A.len[q];
     const float rq = A.rn[q];
-    for (int e = w; e < m; e += RW) {
-      const int c = A.col[a + e];
-      const float v = A.val[a + e] * rq;
-      const int64_t p0 = A.colptr[c], p1 = A.colptr[c + 1];
-      for (int64_t p = p0 + lane; p < p1; p += kWarp) {
-        const float prod = v * A.csc_val[p];
-        atomicAdd(&acc[A.csc_row[p]], __float2uint_rn(prod * kFix));
+    // Warp w takes entries w, w + RW, ...; the next entry's column bounds are
+    // loaded while the current column is added, four column steps per round.
+    {
+      int e = w;
+      float v = 0.f;
+      int64_t p0 = 0, p1 = 0;
+      if (e < m) {
+        const int c = A.col[a + e];
+        v = A.val[a + e] * rq;
+        p0 = A.colptr[c];
+        p1 = A.colptr[c + 1];
+      }
+      while (e < m) {
+        const int en = e + RW;
+        float vn = 0.f;
+        int64_t n0 = 0, n1 = 0;
+        if (en < m) {
+          const int cn = A.col[a + en];
+          vn = A.val[a + en] * rq;
+          n0 = A.colptr[cn];
+          n1 = A.colptr[cn + 1];
+        }
+        for (int64_t p = p0 + lane; p < p1; p += 4 * kWarp) {
+          int r[4];
+          float x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t pp = p + u * kWarp;
+            r[u] = pp < p1 ? A.csc_row[pp] : -1;
+            x[u] = pp < p1 ? A.csc_val[pp] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float prod = v * x[u];
+            if (r[u] >= 0) atomicAdd(&acc[r[u]], __float2uint_rn(prod * kFix));
+          }
+        }
+        e = en;
+        v = vn;
+        p0 = n0;
+        p1 = n1;
       }
     }
     __syncthreads();
@@ -226,6 +260,8 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     int off;
     const int cnt = block_exscan(lane == 0 ? mine : 0, tmp, off);  // one count per warp (lane 0)
     off = __shfl_sync(kFull, off, 0);
+    // Zeros before this warp's words: all earlier words are whole, so 32 w0 - (non-zeros before).
+    const int64_t zeros_before = int64_t(w0) * 32 - off;
     const bool small = cnt <= SORT_CAP && A.acc_smem && ng >= 2 * int64_t(cnt);
     uint32_t* k0 = small ? skeys : gk0;
     uint32_t* v0 = small ? svals : gv0;
@@ -258,15 +294,7 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
       A.out_dist[q * T + p] = 1.0f - s;
     }
     if (T > cnt) {
-      int z = 0;
-      for (int wd = w0; wd < w1; ++wd) {
-        const int valid = int(tmin<int64_t>(32, ng - int64_t(wd) * 32));
-        const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
-        z += __popc(~bits[wd] & vm);
-      }
-      int zoff;
-      block_exscan(lane == 0 ? z : 0, tmp, zoff);
-      int64_t pos = cnt + __shfl_sync(kFull, zoff, 0);
+      int64_t pos = cnt + zeros_before;
       for (int wd = w0; wd < w1 && pos < T; ++wd) {
         const int valid = int(tmin<int64_t>(32, ng - int64_t(wd) * 32));
         const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
