@@ -102,6 +102,7 @@ def test_clustered_shapes(R, nq, ng, d, c, k1, k2, layers):
     (30, 500, 128, 26, 7, 0, 0),    # no propagation
     (64, 900, 128, 26, 7, 2, 17),   # truncated output lists
     (5, 1000, 16, 8, 8, 4, 0),      # k2 = k1, four layers
+    (40, 800, 64, 48, 40, 2, 0),    # more messages per row than lanes in a warp (k2 >= 32)
 ])
 def test_edge_shapes(R, nq, ng, d, k1, k2, layers, topk):
     rng = np.random.default_rng(nq * 1000 + ng)
