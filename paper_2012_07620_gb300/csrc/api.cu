@@ -109,11 +109,16 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
     }
     b.ahi = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
     b.alo = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
-    b.part3_s = c.take<float>(size_t(n) * sh.P3 * sh.K);
-    b.part3_i = c.take<int32_t>(size_t(n) * sh.P3 * sh.K);
+    const size_t p3 = size_t(std::max(sh.P3, sh.P3g));
+    b.part3_s = c.take<float>(size_t(n) * p3 * sh.K);
+    b.part3_i = c.take<int32_t>(size_t(n) * p3 * sh.K);
     b.row_floor3 = c.take<int>(size_t(n));
     b.fb2_rows = c.take<int32_t>(size_t(n));
     b.fb2_count = c.take<int32_t>(4);
+    if (precision == RERANK_PREC_FP8) {
+      b.fb3_rows = c.take<int32_t>(size_t(n));
+      b.fb3_count = c.take<int32_t>(4);
+    }
   }
   b.row_floor = c.take<int>(size_t(n));
   b.nb4 = c.take<int32_t>(4 * size_t(n));
@@ -230,6 +235,7 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
   k_status_reset<<<1, 64, 0, s>>>(status);
   RR_CUDA(cudaMemsetAsync(b.fb_count, 0, sizeof(int32_t), s));
   if (b.fb2_count) RR_CUDA(cudaMemsetAsync(b.fb2_count, 0, sizeof(int32_t), s));
+  if (b.fb3_count) RR_CUDA(cudaMemsetAsync(b.fb3_count, 0, sizeof(int32_t), s));
   const void* dq = j.xq;
   const void* dg = j.xg;
   if (sh.host_in) {
@@ -282,15 +288,34 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     // |S' - S| is ~1e-5 instead of ~1e-3, enough for rows whose k1-th
     // neighbour sits among many near-equal scores.
     nl += launch_gather_rows(b.fb_rows, b.fb_count, b.xhi, b.xlo, b.ahi, b.alo, sh.n, sh.dp, s);
-    const int r = launch_sim_tc_split_topk(sh, sh.P3, b.ahi, b.alo, b.xhi, b.xlo, b.fb_rows, b.fb_count,
+    const int32_t* split_rows = b.fb_rows;
+    const int32_t* split_count = b.fb_count;
+    if (prec == RERANK_PREC_FP8) {
+      // FP8 leaves most rows uncertified (its bound is ~0.07): a BF16 stage
+      // (the hi copies, one product, bound ~2e-3) first, the hi/lo split only
+      // for what that cannot certify.
+      const int rg = launch_sim_tc_gather_topk(sh, sh.P3g, b.ahi, b.xhi, b.fb_rows, b.fb_count, b.row_floor3,
+                                               b.part3_s, b.part3_i, status, ctx->sm_count, s);
+      if (rg < 0) return RERANK_ECUDA;
+      nl += rg;
+      ErrModel eh = em;
+      eh.kind = 3;
+      eh.eps = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
+      nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3g, eh, b.fb_rows, b.fb_count, false,
+                          b.knn_idx, b.knn_score, b.fb3_rows, b.fb3_count, status, s, -1, kStFallbackMid);
+      nl += launch_gather_rows(b.fb3_rows, b.fb3_count, b.xhi, b.xlo, b.ahi, b.alo, sh.n, sh.dp, s);
+      split_rows = b.fb3_rows;
+      split_count = b.fb3_count;
+    }
+    const int r = launch_sim_tc_split_topk(sh, sh.P3, b.ahi, b.alo, b.xhi, b.xlo, split_rows, split_count,
                                            b.row_floor3, b.part3_s, b.part3_i, status, ctx->sm_count, s);
     if (r < 0) return RERANK_ECUDA;
     nl += r;
     ErrModel e3 = em;
     e3.kind = 2;
     e3.eps = (3 * (sh.dp / 16) + 32) * 2.0 * kU32 + 8.0 * kU32;
-    nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3, e3, b.fb_rows, b.fb_count, false,
-                        b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, status, s);
+    nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3, e3, split_rows, split_count, false,
+                        b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, status, s, -1, kStFallback2);
     exact_rows = b.fb2_rows;
     exact_count = b.fb2_count;
     RR_CUDA(cudaGetLastError());
@@ -459,6 +484,7 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
   sh.P = std::min(chunks, 32 / lpc) * lpc;
   // The recheck covers an unknown, usually small, set of rows: many short chunks keep every SM busy.
   sh.P3 = tc ? int(std::min<int64_t>(32 / lpc3, sh.np / 256)) * lpc3 : 0;
+  sh.P3g = prec == RERANK_PREC_FP8 ? int(std::min<int64_t>(32 / lpc, sh.np / 256)) * lpc : 0;
   // Capacity of a propagation layer: sum over rows of ub_i <= min(n, sum_j len_j).
   // n^2 bounds it exactly for small graphs; otherwise a generous guess, grown on overflow.
   int64_t guess = std::max<int64_t>(2 * sh.n * k1, std::min<int64_t>(sh.n * sh.n, sh.n * int64_t(k2 + 1) * 160));

@@ -73,6 +73,8 @@ struct Buffers {
   int* row_floor3 = nullptr;     // n
   int32_t* fb2_rows = nullptr;   // n: rows left for the exact scan
   int32_t* fb2_count = nullptr;
+  int32_t* fb3_rows = nullptr;   // n: FP8 path, rows left after the BF16 stage
+  int32_t* fb3_count = nullptr;
   int* row_floor = nullptr;      // n, shared K-th best per row (similarity kernels)
   int32_t* nb4 = nullptr;        // 4n: best candidates per row (processing order)
   int32_t* label = nullptr;      // n
@@ -125,7 +127,8 @@ struct Shape {
   int64_t nq = 0, ng = 0, n = 0, np = 0;
   int d = 0, dp = 0, dtype = 0;
   int k1 = 0, k2 = 0, layers = 0, K = 0, P = 0;
-  int P3 = 0;              // column chunks of the hi/lo recheck
+  int P3 = 0;              // candidate lists per row of the hi/lo recheck
+  int P3g = 0;             // FP8 path: lists per row of the BF16 recheck stage
   int64_t topk = 0;
   bool host_in = false, host_out = false;
   bool knn_only = false;
@@ -216,9 +219,15 @@ int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, 
                              const int32_t* count, int* row_floor, float* part_s, int32_t* part_i,
                              long long* status, int sm_count, cudaStream_t s);
 
+// Gathered rows rows[0 .. *count) (their BF16 hi copies in ahi) against every
+// column's hi copy, one product: the middle stage of the FP8 path's recheck.
+int launch_sim_tc_gather_topk(const Shape& sh, int P, const __nv_bfloat16* ahi, const __nv_bfloat16* bhi,
+                              const int32_t* rows, const int32_t* count, int* row_floor, float* part_s,
+                              int32_t* part_i, long long* status, int sm_count, cudaStream_t s);
+
 // Bound on |approximate score - S_ij| used to certify a row's candidate list.
 struct ErrModel {
-  int kind = 0;                  // 0: eps only; 1: one quantised copy; 2: hi/lo split
+  int kind = 0;                  // 0: eps only; 1: one quantised copy; 2: hi/lo split; 3: the hi copy
   double eps = 0.0;              // accumulation and rounding part
   const float* err = nullptr;    // 3 x np per-row bounds (see Buffers::err)
   const float* emax = nullptr;
@@ -230,7 +239,8 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
                    const double* norm, const float* part_s, const int32_t* part_i, int P, const ErrModel& em,
                    const int32_t* rows, const int32_t* count, bool part_by_row,
                    int32_t* knn_idx, float* knn_score, int32_t* fb_rows, int32_t* fb_count,
-                   long long* status, cudaStream_t s, int64_t grid_rows = -1);  // grid_rows: bound on the row count
+                   long long* status, cudaStream_t s, int64_t grid_rows = -1,  // grid_rows: bound on the row count
+                   int fb_stat = -1);  // status slot counting the rows passed on (-1: by the row set)
 size_t tc_smem_bytes();
 int tc_kmax();
 // Candidate lists per row and column chunk written by the tensor-core kernels

@@ -55,7 +55,10 @@ constexpr int EG_MAX = 2;
 constexpr int threads_of(int eg) { return 64 + 128 * eg; }  // TMA warp, MMA warp, 4 epilogue warps per group
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
-enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2 };
+// BF16 / FP8: one matrix against itself (or a rectangular block);
+// SPLIT: gathered rows, hi/lo products; GATHER: gathered rows, one BF16 product.
+enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2, MODE_GATHER = 3 };
+constexpr bool gathered(int mode) { return mode == MODE_SPLIT || mode == MODE_GATHER; }
 
 struct alignas(1024) TcSmem {
   uint8_t a[STAGES][A_BYTES];
@@ -105,8 +108,8 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort = &sm.abort;
   constexpr int SEGS = MODE == MODE_SPLIT ? 3 : 1;
-  const int64_t nrows = MODE == MODE_SPLIT ? int64_t(*A.count) : A.a_rows;
-  const int row_blocks = MODE == MODE_SPLIT ? int((nrows + TBM - 1) / TBM) : A.row_blocks;
+  const int64_t nrows = gathered(MODE) ? int64_t(*A.count) : A.a_rows;
+  const int row_blocks = gathered(MODE) ? int((nrows + TBM - 1) / TBM) : A.row_blocks;
   const int items = row_blocks * A.chunks;
   const int kb_total = A.kblocks * SEGS;
 
@@ -252,7 +255,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       item_range(A, row_blocks, item, rb, chunk, t0, t1);
       const int64_t arow = int64_t(rb) * TBM + r;   // row of the A operand
       const bool live = arow < nrows;
-      const int64_t grow = MODE == MODE_SPLIT ? (live ? int64_t(A.rows[arow]) : -1) : A.row0 + arow;  // vertex
+      const int64_t grow = gathered(MODE) ? (live ? int64_t(A.rows[arow]) : -1) : A.row0 + arow;  // vertex
 #pragma unroll
       for (int j = 0; j < KL; ++j) {
         ls[j] = -FLT_MAX;
@@ -531,6 +534,32 @@ int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, 
   A.status = status;
   A.stall = stall_hook();
   launch_mode<MODE_SPLIT>(a0, a1, b0, b1, A, eg, sm_count, s);
+  return 1;
+}
+
+int launch_sim_tc_gather_topk(const Shape& sh, int P, const __nv_bfloat16* ahi, const __nv_bfloat16* bhi,
+                              const int32_t* rows, const int32_t* count, int* row_floor, float* part_s,
+                              int32_t* part_i, long long* status, int sm_count, cudaStream_t s) {
+  CUtensorMap a0, b0;
+  if (!make_map(&a0, ahi, sh.np, sh.dp, false) || !make_map(&b0, bhi, sh.np, sh.dp, false)) return -1;
+  cudaMemsetAsync(row_floor, kFloorResetByte, sizeof(int) * size_t(sh.n), s);
+  TcArgs A{};
+  A.n = sh.n;
+  A.row_blocks = 0;
+  A.col_tiles = int(sh.np / TBN);
+  const int eg = tc_lists_per_chunk(sh.dp, 1);
+  A.chunks = P / eg;  // P counts lists per row
+  if (A.chunks < 1 || A.chunks * eg != P || A.chunks > A.col_tiles) return -1;
+  A.kblocks = sh.dp / 64;
+  A.K = sh.K;
+  A.rows = rows;
+  A.count = count;
+  A.row_floor = row_floor;
+  A.part_s = part_s;
+  A.part_i = part_i;
+  A.status = status;
+  A.stall = stall_hook();
+  launch_mode<MODE_GATHER>(a0, a0, b0, b0, A, eg, sm_count, s);
   return 1;
 }
 

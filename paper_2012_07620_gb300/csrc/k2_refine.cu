@@ -359,6 +359,11 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
     // one quantised copy q = x - e:  |<q_i,q_j> - <x_i,x_j>| <= e_i + e_max + e_i e_max
     const double ei = em.err[i], emx = em.emax[0];
     eps_g += ei + emx + ei * emx;
+  } else if (em.kind == 3) {
+    // the BF16 hi copy: ||x - hi|| = ||lo + r|| <= ||lo|| + ||r||, as for one quantised copy
+    const double ei = double(em.err[em.np + i]) + double(em.err[2 * em.np + i]);
+    const double emx = double(em.emax[1]) + double(em.emax[2]);
+    eps_g += ei + emx + ei * emx;
   } else if (em.kind == 2) {
     // x = hi + lo + r exactly, S' = hi.hi + lo.hi + hi.lo, so S - S' = lo_i.lo_j + r_i.x_j +
     // (hi_i + lo_i).r_j and |S' - S| <= ||lo_i|| lo_max + ||r_i|| + r_max (with slack for ||x|| ~ 1):
@@ -466,12 +471,12 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
                    const float* part_s, const int32_t* part_i, int P, const ErrModel& em, const int32_t* rows,
                    const int32_t* count, bool part_by_row, int32_t* knn_idx, float* knn_score,
                    int32_t* fb_rows, int32_t* fb_count,
-                   long long* status, cudaStream_t s, int64_t grid_rows) {
+                   long long* status, cudaStream_t s, int64_t grid_rows, int fb_stat) {
   RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
   const int64_t g = grid_rows > 0 && grid_rows < sh.n ? grid_rows : sh.n;
   const unsigned blocks = unsigned((g + WPB - 1) / WPB);
   // First pass: uncertified rows go to the recheck; a recheck's failures go to the exact scan.
-  const int stat = (rows && !part_by_row) ? kStFallback2 : kStFallback;
+  const int stat = fb_stat >= 0 ? fb_stat : ((rows && !part_by_row) ? kStFallback2 : kStFallback);
   // Row i in registers: 4 float4s per lane up to dp = 512, 16 up to 2048.
   if (sh.dp <= 512)
     k2_refine<4><<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em, rescore_eps(sh.dp),
