@@ -517,7 +517,7 @@ rerank_status run_with_retry(rerank_ctx* ctx, const void* xq, const void* xg, in
   return st;
 }
 
-constexpr int kBatchStreams = 8;
+constexpr int kBatchStreams = 16;
 
 rerank_status ensure_streams(rerank_ctx* ctx) {
   if (!ctx->streams.empty()) return RERANK_OK;
