@@ -130,9 +130,15 @@ typedef struct {
  * compute it; the paper defines one instance at a time, Sec. 3.3) in one call.
  * The instances share one workspace block and run concurrently on the GPU:
  * their stages are enqueued on internal streams forked from `stream` and
- * joined back into it, largest instances first.  The call reads every
- * instance's status with one device-to-host copy and one synchronisation;
- * an instance whose propagation buffers overflowed is rerun alone.
+ * joined back into it, largest instances first.  With the BF16 / FP8
+ * precisions the similarity + top-K stage of up to 64 instances runs as one
+ * persistent tensor-core launch whose CTAs walk the work items of all of
+ * them.  A call whose inputs and outputs are all device or pinned host memory
+ * is captured as a CUDA graph the second time its pointers and shapes occur
+ * and replayed by later calls with the same ones (the context keeps the 4
+ * most recently used graphs).
+ * The call reads every instance's status with one synchronisation; an
+ * instance whose propagation buffers overflowed is rerun alone.
  *   jobs    array of njobs instances; inputs and outputs may be host or device
  *           memory, as for rerank_run
  * Returns OK when every instance succeeded, else the first failing status

@@ -217,7 +217,7 @@ cudaError_t ensure_copy_stream(rerank_ctx* ctx) {
 }
 
 rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches,
-                          bool copy_overlap) {
+                          bool copy_overlap, int phases) {
   const Shape& sh = j.sh;
   const Buffers& b = j.b;
   long long* status = j.st;
@@ -231,46 +231,57 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     nvtxMarkA(name);
     if (tm) tm->mark(name);
   };
-  int64_t nl = 1;
-  k_status_reset<<<1, 64, 0, s>>>(status);
-  RR_CUDA(cudaMemsetAsync(b.fb_count, 0, sizeof(int32_t), s));
-  if (b.fb2_count) RR_CUDA(cudaMemsetAsync(b.fb2_count, 0, sizeof(int32_t), s));
-  if (b.fb3_count) RR_CUDA(cudaMemsetAsync(b.fb3_count, 0, sizeof(int32_t), s));
-  const void* dq = j.xq;
-  const void* dg = j.xg;
-  if (sh.host_in) {
-    const size_t es = type_size(sh.dtype);
-    RR_CUDA(cudaMemcpyAsync(b.xq, j.xq, size_t(sh.nq) * sh.d * es, cudaMemcpyHostToDevice, s));
-    if (sh.ng) RR_CUDA(cudaMemcpyAsync(b.xg, j.xg, size_t(sh.ng) * sh.d * es, cudaMemcpyHostToDevice, s));
-    dq = b.xq;
-    dg = b.xg;
-    mark("h2d");
-  }
+  int64_t nl = 0;
+  const void* dq = sh.host_in ? b.xq : j.xq;
+  const void* dg = sh.host_in ? b.xg : j.xg;
   const int prec = ctx->cfg.precision;
-  nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xhi, b.xlo, b.xscale, b.err, b.emax, prec, status, s);
-  mark("normalize");
+  if (phases & kPhasePre) {
+    k_status_reset<<<1, 64, 0, s>>>(status);
+    ++nl;
+    RR_CUDA(cudaMemsetAsync(b.fb_count, 0, sizeof(int32_t), s));
+    if (b.fb2_count) RR_CUDA(cudaMemsetAsync(b.fb2_count, 0, sizeof(int32_t), s));
+    if (b.fb3_count) RR_CUDA(cudaMemsetAsync(b.fb3_count, 0, sizeof(int32_t), s));
+    if (sh.host_in) {
+      const size_t es = type_size(sh.dtype);
+      RR_CUDA(cudaMemcpyAsync(b.xq, j.xq, size_t(sh.nq) * sh.d * es, cudaMemcpyHostToDevice, s));
+      if (sh.ng) RR_CUDA(cudaMemcpyAsync(b.xg, j.xg, size_t(sh.ng) * sh.d * es, cudaMemcpyHostToDevice, s));
+      mark("h2d");
+    }
+    nl += launch_normalize(sh, dq, dg, b.xhat, b.norm, b.xlow, b.xhi, b.xlo, b.xscale, b.err, b.emax, prec, status,
+                           s);
+    mark("normalize");
+  }
   ErrModel em;
   em.err = b.err;
   em.emax = b.emax;
   em.np = sh.np;
   if (prec == RERANK_PREC_FP32) {
-    nl += launch_sim_fp32_topk(sh, b.xhat, b.row_floor, b.part_s, b.part_i, ctx->sm_count, s);
     // One FMA chain of dp terms over unit rows.
     em.kind = 0;
     em.eps = (sh.dp + 10) * kU32 * 1.01;
   } else {
-    const int r = launch_sim_tc_topk(sh, b.xlow, prec == RERANK_PREC_FP8, b.xscale, b.row_floor, b.part_s, b.part_i,
-                                     status, ctx->sm_count, s);
-    if (r < 0) return RERANK_ECUDA;
-    nl += r;
     // Quantisation error enters per row; on top: the FP32 accumulation of dp/16
     // (BF16) or dp/32 (FP8) tensor-core partial sums, each charged 2u, the
     // rounding of the unit rows (4u) and of the FP8 scale products (2u).
     em.kind = 1;
     em.eps = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
   }
-  RR_CUDA(cudaGetLastError());
-  mark("similarity_topk");
+  if (phases & kPhaseSim) {
+    if (prec == RERANK_PREC_FP32) {
+      nl += launch_sim_fp32_topk(sh, b.xhat, b.row_floor, b.part_s, b.part_i, ctx->sm_count, s);
+    } else {
+      const int r = launch_sim_tc_topk(sh, b.xlow, prec == RERANK_PREC_FP8, b.xscale, b.row_floor, b.part_s,
+                                       b.part_i, status, ctx->sm_count, s);
+      if (r < 0) return RERANK_ECUDA;
+      nl += r;
+    }
+    RR_CUDA(cudaGetLastError());
+    mark("similarity_topk");
+  }
+  if (!(phases & kPhasePost)) {
+    *launches += nl;
+    return RERANK_OK;
+  }
   const int32_t* order = nullptr;
   if (sh.tune.refine_order) {
     nl += launch_cluster_order(sh, b.part_s, b.part_i, b.nb4, b.label, b.ord_cnt, b.ord_start, b.ord_fill, b.order,
@@ -544,6 +555,95 @@ rerank_status ensure_host_status(rerank_ctx* ctx, size_t count) {
   return RERANK_OK;
 }
 
+rerank_status ensure_host_stage(rerank_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->h_stage_bytes) return RERANK_OK;
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  ctx->h_stage = nullptr;
+  ctx->h_stage_bytes = 0;
+  RR_CUDA(cudaMallocHost(&ctx->h_stage, bytes));
+  ctx->h_stage_bytes = bytes;
+  return RERANK_OK;
+}
+
+// Memory the GPU cannot reach from a graph's copy nodes without staging.
+bool is_pageable(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return a.type == cudaMemoryTypeUnregistered;
+}
+
+// Every field of a planned instance: together with the job's pointers and
+// workspace offset they fix everything a batched call enqueues for it.
+void shape_key(const Shape& sh, std::vector<int64_t>& k) {
+  const int64_t v[] = {sh.nq, sh.ng, sh.n, sh.np, sh.d, sh.dp, sh.dtype, sh.k1, sh.k2, sh.layers, sh.K, sh.P, sh.P3,
+                       sh.P3g, sh.topk, sh.host_in, sh.host_out, sh.knn_only, sh.ext_feat, sh.cap_h, sh.cap_csc,
+                       sh.hash_slots, sh.rank_ctas, sh.rank_scratch_per_cta, sh.tune.sim_chunks, sh.tune.prop_warps,
+                       sh.tune.refine_order, sh.tune.rescore_m, sh.tune.rank_threads};
+  k.insert(k.end(), std::begin(v), std::end(v));
+}
+
+uint64_t key_hash(const std::vector<int64_t>& k) {
+  uint64_t h = 1469598103934665603ull;  // FNV-1a over the 64-bit words
+  for (int64_t v : k) h = (h ^ uint64_t(v)) * 1099511628211ull;
+  return h;
+}
+
+void free_graph(BatchGraph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->stage) cudaFreeHost(g->stage);
+  delete g;
+}
+
+// Capture what `enqueue` issues into a new graph of the context's cache
+// (evicting the least recently used one beyond kMaxGraphs).  *out stays null
+// when the capture itself was refused (the caller then enqueues directly).
+constexpr size_t kMaxGraphs = 4;
+template <class F>
+rerank_status capture_batch_graph(rerank_ctx* ctx, std::vector<int64_t>&& key, size_t stage_bytes, int64_t* nl,
+                                  F& enqueue, BatchGraph** out) {
+  *out = nullptr;
+  if (!ctx->cap_stream) RR_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  BatchGraph* g = new BatchGraph;
+  g->key = std::move(key);
+  if (cudaMallocHost(&g->stage, stage_bytes ? stage_bytes : 16) != cudaSuccess) {
+    g->stage = nullptr;
+    free_graph(g);
+    return cuda_fail(cudaGetLastError(), "cudaMallocHost");
+  }
+  *nl = 0;
+  if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cudaGetLastError();
+    free_graph(g);
+    return RERANK_OK;
+  }
+  const rerank_status st = enqueue(ctx->cap_stream, g->stage);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  cudaError_t ei = cudaErrorUnknown;
+  if (st == RERANK_OK && ec == cudaSuccess && graph) ei = cudaGraphInstantiate(&g->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (st != RERANK_OK || ei != cudaSuccess) {
+    cudaGetLastError();
+    g->exec = nullptr;
+    free_graph(g);
+    return st;
+  }
+  g->launches = *nl;
+  if (ctx->graphs.size() >= kMaxGraphs) {
+    auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                [](const BatchGraph* a, const BatchGraph* b) { return a->stamp < b->stamp; });
+    free_graph(*lru);
+    ctx->graphs.erase(lru);
+  }
+  ctx->graphs.push_back(g);
+  *out = g;
+  return RERANK_OK;
+}
+
 // Rough device cost of an instance, used to spread instances over the streams.
 double job_cost(const Shape& sh) {
   return double(sh.np) * double(sh.np) * double(sh.dp) + 4.0e4 * double(sh.n) * double(sh.k1);
@@ -568,12 +668,23 @@ rerank_status run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, cudaStream
     off[size_t(i)] = total;
     total += ((st_bytes + 255) & ~size_t(255)) + need;
   }
+  // Tensor-core precisions: the similarity stage of all instances runs as
+  // persistent launches over many instances (their tables live here).
+  const bool tc_batch = ctx->cfg.precision != RERANK_PREC_FP32;
+  const size_t inst_bytes = tc_batch_inst_bytes() * size_t(njobs);
+  total = (total + 255) & ~size_t(255);
+  const size_t inst_off = total;
+  if (tc_batch) total += inst_bytes;
   rerank_status st = ensure_workspace(ctx, total);
   if (st != RERANK_OK) return st;
   st = ensure_streams(ctx);
   if (st != RERANK_OK) return st;
   st = ensure_host_status(ctx, size_t(njobs) * kStCount);
   if (st != RERANK_OK) return st;
+  if (tc_batch) {
+    st = ensure_host_stage(ctx, inst_bytes);
+    if (st != RERANK_OK) return st;
+  }
   for (int i = 0; i < njobs; ++i) {
     JobRun& j = runs[size_t(i)];
     j.st = reinterpret_cast<long long*>(ctx->ws + off[size_t(i)]);
@@ -594,25 +705,142 @@ rerank_status run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, cudaStream
   });
   const int ns = std::min<int>(kBatchStreams, njobs);
   std::vector<double> load(static_cast<size_t>(ns), 0.0);
-  RR_CUDA(cudaEventRecord(ctx->events[0], s));
-  for (int k = 0; k < ns; ++k) RR_CUDA(cudaStreamWaitEvent(ctx->streams[size_t(k)], ctx->events[0], 0));
-  int64_t nl = 0;
+  std::vector<int> lane(static_cast<size_t>(njobs), 0);
   for (int i : idx) {
     int k = 0;
     for (int t = 1; t < ns; ++t)
       if (load[size_t(t)] < load[size_t(k)]) k = t;
     load[size_t(k)] += job_cost(runs[size_t(i)].sh);
-    st = enqueue_job(ctx, runs[size_t(i)], ctx->streams[size_t(k)], nullptr, &nl);
-    if (st != RERANK_OK) break;
+    lane[size_t(i)] = k;
   }
-  for (int k = 0; k < ns; ++k) {
-    RR_CUDA(cudaEventRecord(ctx->events[size_t(1 + k)], ctx->streams[size_t(k)]));
-    RR_CUDA(cudaStreamWaitEvent(s, ctx->events[size_t(1 + k)], 0));
+  int64_t nl = 0;
+  // Everything the call enqueues, from stream `o`: fork onto the streams,
+  // each phase of every instance on its stream, join back into `o`; the
+  // status blocks are copied to the host last.  `stage`: pinned memory for the
+  // instance tables of the batched similarity launches.
+  auto enqueue_all = [&](cudaStream_t o, void* stage) -> rerank_status {
+    auto fan_out = [&](int phases) -> rerank_status {
+      RR_CUDA(cudaEventRecord(ctx->events[0], o));
+      for (int k = 0; k < ns; ++k) RR_CUDA(cudaStreamWaitEvent(ctx->streams[size_t(k)], ctx->events[0], 0));
+      rerank_status r = RERANK_OK;
+      for (int i : idx) {
+        r = enqueue_job(ctx, runs[size_t(i)], ctx->streams[size_t(lane[size_t(i)])], nullptr, &nl, false, phases);
+        if (r != RERANK_OK) break;
+      }
+      for (int k = 0; k < ns; ++k) {
+        RR_CUDA(cudaEventRecord(ctx->events[size_t(1 + k)], ctx->streams[size_t(k)]));
+        RR_CUDA(cudaStreamWaitEvent(o, ctx->events[size_t(1 + k)], 0));
+      }
+      return r;
+    };
+    rerank_status r = RERANK_OK;
+    if (!tc_batch) {
+      r = fan_out(kPhaseAll);
+    } else {
+      r = fan_out(kPhasePre);
+      if (r == RERANK_OK) {
+        // Similarity + top-K: instances with the same epilogue layout share a
+        // launch, largest first (up to the launch's instance limit).
+        const bool fp8 = ctx->cfg.precision == RERANK_PREC_FP8;
+        std::vector<TcBatchInst> group;
+        size_t used = 0;
+        for (int eg = 1; eg <= 2 && r == RERANK_OK; ++eg) {
+          group.clear();
+          for (size_t p = 0; p <= idx.size(); ++p) {
+            const bool end = p == idx.size();
+            if (!end) {
+              const JobRun& j = runs[size_t(idx[p])];
+              if (tc_lists_per_chunk(j.sh.dp, 1) != eg) continue;
+              TcBatchInst t{};
+              t.xlow = j.b.xlow;
+              t.n = j.sh.n;
+              t.np = j.sh.np;
+              t.dp = j.sh.dp;
+              t.P = j.sh.P;
+              t.K = j.sh.K;
+              t.inv_scale = j.b.xscale;
+              t.row_floor = j.b.row_floor;
+              t.part_s = j.b.part_s;
+              t.part_i = j.b.part_i;
+              t.status = j.st;
+              group.push_back(t);
+            }
+            if (!group.empty() && (end || int(group.size()) == tc_batch_max_inst())) {
+              const int k = launch_sim_tc_batch(group.data(), int(group.size()), fp8, ctx->ws + inst_off + used,
+                                                static_cast<uint8_t*>(stage) + used, ctx->sm_count, o);
+              if (k < 0) {
+                r = RERANK_ECUDA;
+                break;
+              }
+              nl += k;
+              used += tc_batch_inst_bytes() * group.size();
+              group.clear();
+            }
+          }
+        }
+        if (r == RERANK_OK) RR_CUDA(cudaGetLastError());
+      }
+      if (r == RERANK_OK) r = fan_out(kPhasePost);
+    }
+    if (r != RERANK_OK) return r;
+    for (int i = 0; i < njobs; ++i)
+      RR_CUDA(cudaMemcpyAsync(ctx->h_batch + size_t(i) * kStCount, runs[size_t(i)].st, st_bytes,
+                              cudaMemcpyDeviceToHost, o));
+    return RERANK_OK;
+  };
+  // A call whose buffers are all device or pinned memory is captured once as a
+  // CUDA graph and replayed by later calls with the same key (thousands of
+  // small launches become one graph launch).
+  bool graphable = true;
+  for (int i = 0; i < njobs && graphable; ++i) {
+    const rerank_job& jb = jobs[i];
+    graphable = !is_pageable(jb.xq) && !is_pageable(jb.xg) && !is_pageable(jb.out_idx) && !is_pageable(jb.out_dist);
   }
-  if (st != RERANK_OK) return st;
-  for (int i = 0; i < njobs; ++i)
-    RR_CUDA(cudaMemcpyAsync(ctx->h_batch + size_t(i) * kStCount, runs[size_t(i)].st, st_bytes,
-                            cudaMemcpyDeviceToHost, s));
+  if (graphable) {
+    std::vector<int64_t> key;
+    key.reserve(size_t(njobs) * 40 + 8);
+    key.push_back(int64_t(reinterpret_cast<uintptr_t>(ctx->ws)));
+    key.push_back(int64_t(total));
+    key.push_back(int64_t(reinterpret_cast<uintptr_t>(ctx->h_batch)));
+    key.push_back(tc_stall_hook());
+    for (int i = 0; i < njobs; ++i) {
+      const rerank_job& jb = jobs[i];
+      key.push_back(int64_t(reinterpret_cast<uintptr_t>(jb.xq)));
+      key.push_back(int64_t(reinterpret_cast<uintptr_t>(jb.xg)));
+      key.push_back(int64_t(reinterpret_cast<uintptr_t>(jb.out_idx)));
+      key.push_back(int64_t(reinterpret_cast<uintptr_t>(jb.out_dist)));
+      key.push_back(int64_t(off[size_t(i)]));
+      shape_key(runs[size_t(i)].sh, key);
+    }
+    BatchGraph* g = nullptr;
+    for (BatchGraph* c : ctx->graphs)
+      if (c->key == key) g = c;
+    if (!g) {
+      // Capture only a key seen before: a one-off call is enqueued directly
+      // and pays no instantiation.
+      const uint64_t h = key_hash(key);
+      const bool seen = std::find(ctx->graph_seen.begin(), ctx->graph_seen.end(), h) != ctx->graph_seen.end();
+      if (seen) {
+        st = capture_batch_graph(ctx, std::move(key), inst_bytes, &nl, enqueue_all, &g);
+        if (st != RERANK_OK) return st;
+      } else {
+        if (ctx->graph_seen.size() >= 16) ctx->graph_seen.erase(ctx->graph_seen.begin());
+        ctx->graph_seen.push_back(h);
+      }
+    }
+    if (g) {
+      g->stamp = ++ctx->graph_clock;
+      RR_CUDA(cudaGraphLaunch(g->exec, s));
+      nl = g->launches;
+    } else {
+      graphable = false;  // the capture was refused: enqueue directly
+    }
+  }
+  if (!graphable) {
+    nl = 0;
+    st = enqueue_all(s, ctx->h_stage);
+    if (st != RERANK_OK) return st;
+  }
   RR_CUDA(cudaStreamSynchronize(s));
   RR_CUDA(cudaGetLastError());
   ctx->launches = nl;
@@ -744,6 +972,9 @@ rerank_status rerank_destroy(rerank_ctx* ctx) {
   for (auto st : ctx->streams) cudaStreamDestroy(st);
   for (auto e : ctx->events) cudaEventDestroy(e);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+  for (BatchGraph* g : ctx->graphs) free_graph(g);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (auto e : ctx->copy_events) cudaEventDestroy(e);
   if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
   delete ctx;

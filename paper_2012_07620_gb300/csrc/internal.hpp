@@ -143,6 +143,17 @@ struct Shape {
 
 struct ServeHandle;  // the request loop of a loaded gallery (serve.cu)
 
+// A batched call captured as a CUDA graph.  key: everything the capture
+// depended on (workspace, pointers, planned shapes); stage: the pinned
+// instance tables its copy nodes upload.
+struct BatchGraph {
+  std::vector<int64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  void* stage = nullptr;
+  int64_t launches = 0;
+  uint64_t stamp = 0;
+};
+
 struct StageTimer {
   bool on = false;
   std::vector<cudaEvent_t> ev;
@@ -184,6 +195,13 @@ struct rerank_ctx {
   std::vector<cudaEvent_t> copy_events;
   long long* h_batch = nullptr;
   size_t h_batch_count = 0;
+  void* h_stage = nullptr;  // pinned: instance tables of batched similarity launches
+  size_t h_stage_bytes = 0;
+  // batched calls replayed as CUDA graphs (least recently used evicted)
+  std::vector<rr::BatchGraph*> graphs;
+  uint64_t graph_clock = 0;
+  std::vector<uint64_t> graph_seen;  // hashes of recent keys not yet captured
+  cudaStream_t cap_stream = nullptr;
   rr::ServeHandle* serve = nullptr;
 };
 
@@ -218,6 +236,27 @@ int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, 
                              const __nv_bfloat16* bhi, const __nv_bfloat16* blo, const int32_t* rows,
                              const int32_t* count, int* row_floor, float* part_s, int32_t* part_i,
                              long long* status, int sm_count, cudaStream_t s);
+
+// One instance of a batched similarity launch: the instance's low-precision
+// copy (np x dp) against itself, P lists of K per row.
+struct TcBatchInst {
+  const void* xlow;
+  int64_t n, np;
+  int dp, P, K;
+  const float* inv_scale;
+  int* row_floor;
+  float* part_s;
+  int32_t* part_i;
+  long long* status;
+};
+// Up to 64 instances with the same tc_lists_per_chunk(dp, 1) in one persistent
+// launch.  insts_dev: ninst * tc_batch_inst_bytes() of device memory; staging:
+// as many bytes of pinned host memory, untouched until the launch has run.
+int launch_sim_tc_batch(const TcBatchInst* in, int ninst, bool fp8, void* insts_dev, void* staging, int sm_count,
+                        cudaStream_t s);
+size_t tc_batch_inst_bytes();
+int tc_batch_max_inst();
+int tc_stall_hook();  // nonzero while the tensor-core kernels' test stall is set
 
 // Gathered rows rows[0 .. *count) (their BF16 hi copies in ahi) against every
 // column's hi copy, one product: the middle stage of the FP8 path's recheck.
@@ -290,8 +329,11 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
                          Shape* out, const Tuning* tune = nullptr);  // tune: override of the table lookup
 // copy_overlap: host outputs are copied back in parts while later queries are
 // ranked (single calls only; batched instances copy on their own stream).
+// phases: which parts to enqueue (status reset, copies in and normalisation /
+// the similarity stage / everything after it).
+enum { kPhasePre = 1, kPhaseSim = 2, kPhasePost = 4, kPhaseAll = 7 };
 rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, StageTimer* tm, int64_t* launches,
-                          bool copy_overlap = false);
+                          bool copy_overlap = false, int phases = kPhaseAll);
 rerank_status map_status(const long long* h, int precision, rerank_info* info, int64_t* need);
 int launch_status_reset(long long* st, cudaStream_t s);
 // Tuning of an instance: the table entry for (precision, d, bucket of n), else defaults.

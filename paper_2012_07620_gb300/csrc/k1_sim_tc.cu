@@ -58,7 +58,7 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 // BF16 / FP8: one matrix against itself (or a rectangular block);
 // SPLIT: gathered rows, hi/lo products; GATHER: gathered rows, one BF16 product.
 enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2, MODE_GATHER = 3 };
-constexpr bool gathered(int mode) { return mode == MODE_SPLIT || mode == MODE_GATHER; }
+__host__ __device__ constexpr bool gathered(int mode) { return mode == MODE_SPLIT || mode == MODE_GATHER; }
 
 struct alignas(1024) TcSmem {
   uint8_t a[STAGES][A_BYTES];
@@ -71,6 +71,23 @@ struct alignas(1024) TcSmem {
   uint64_t done;
   uint32_t tmem_base;
   int abort;
+};
+
+// Batched launches: up to kMaxBatchInst instances, each a matrix against
+// itself; their tensor maps travel as one kernel parameter.
+constexpr int kMaxBatchInst = 64;
+struct TcMaps {
+  CUtensorMap m[kMaxBatchInst];
+};
+struct TcInst {
+  int64_t n;                // rows = columns of the instance
+  int row_blocks, col_tiles, chunks, kblocks, K;
+  int item_begin;           // first item of the instance in the launch's item space
+  const float* inv_scale;
+  int* row_floor;
+  float* part_s;
+  int32_t* part_i;
+  long long* status;
 };
 
 struct TcArgs {
@@ -88,21 +105,92 @@ struct TcArgs {
   float* part_s;
   int32_t* part_i;
   long long* status;
+  const TcInst* insts;      // batched launch: the instances (device memory), else null
+  int ninst, items_total;
 };
 
-__device__ __forceinline__ void item_range(const TcArgs& A, int row_blocks, int item, int& rb, int& chunk, int& t0,
-                                           int& t1) {
-  rb = item % row_blocks;
-  chunk = item / row_blocks;
-  t0 = int(int64_t(chunk) * A.col_tiles / A.chunks);
-  t1 = int(int64_t(chunk + 1) * A.col_tiles / A.chunks);
+// One work item (a row block against a chunk of column tiles) with the
+// parameters of its instance.
+struct TcItem {
+  const CUtensorMap* ma0;
+  const CUtensorMap* ma1;
+  const CUtensorMap* mb0;
+  const CUtensorMap* mb1;
+  int rb, chunk, t0, t1, kblocks, K, chunks;
+  int64_t n, nrows, row0, col0;
+  const float* inv_scale;
+  int* row_floor;
+  float* part_s;
+  int32_t* part_i;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ void get_item(const TcArgs& A, const CUtensorMap* ma0, const CUtensorMap* ma1,
+                                         const CUtensorMap* mb0, const CUtensorMap* mb1, const CUtensorMap* bmaps,
+                                         int row_blocks, int64_t nrows, int item, TcItem& it) {
+  if (!BATCH) {
+    it.ma0 = ma0;
+    it.ma1 = ma1;
+    it.mb0 = mb0;
+    it.mb1 = mb1;
+    it.rb = item % row_blocks;
+    it.chunk = item / row_blocks;
+    it.t0 = int(int64_t(it.chunk) * A.col_tiles / A.chunks);
+    it.t1 = int(int64_t(it.chunk + 1) * A.col_tiles / A.chunks);
+    it.kblocks = A.kblocks;
+    it.K = A.K;
+    it.chunks = A.chunks;
+    it.n = A.n;
+    it.nrows = nrows;
+    it.row0 = A.row0;
+    it.col0 = A.col0;
+    it.inv_scale = A.inv_scale;
+    it.row_floor = A.row_floor;
+    it.part_s = A.part_s;
+    it.part_i = A.part_i;
+  } else {
+    int lo = 0, hi = A.ninst - 1;  // last instance whose items begin at or before `item`
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (A.insts[mid].item_begin <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const TcInst& I = A.insts[lo];
+    const int local = item - I.item_begin;
+    it.ma0 = it.ma1 = it.mb0 = it.mb1 = bmaps + lo;
+    it.rb = local % I.row_blocks;
+    it.chunk = local / I.row_blocks;
+    it.t0 = int(int64_t(it.chunk) * I.col_tiles / I.chunks);
+    it.t1 = int(int64_t(it.chunk + 1) * I.col_tiles / I.chunks);
+    it.kblocks = I.kblocks;
+    it.K = I.K;
+    it.chunks = I.chunks;
+    it.n = I.n;
+    it.nrows = I.n;
+    it.row0 = 0;
+    it.col0 = 0;
+    it.inv_scale = I.inv_scale;
+    it.row_floor = I.row_floor;
+    it.part_s = I.part_s;
+    it.part_i = I.part_i;
+  }
+}
+
+// Timeout: every instance of the launch reports it.
+template <bool BATCH>
+__device__ void report_timeout(const TcArgs& A) {
+  if (!BATCH) {
+    set_error(A.status, kErrTimeout);
+  } else {
+    for (int k = 0; k < A.ninst; ++k) set_error(A.insts[k].status, kErrTimeout);
+  }
 }
 
 
-template <int MODE, int KL, int EGROUPS>
-__global__ void __launch_bounds__(threads_of(EGROUPS), 1)
-k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-           const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs A) {
+
+template <int MODE, int KL, int EGROUPS, bool BATCH>
+__device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMap* pA1, const CUtensorMap* pB0,
+                                        const CUtensorMap* pB1, const CUtensorMap* bmaps, const TcArgs& A) {
   extern __shared__ uint8_t smem_raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -110,8 +198,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
   constexpr int SEGS = MODE == MODE_SPLIT ? 3 : 1;
   const int64_t nrows = gathered(MODE) ? int64_t(*A.count) : A.a_rows;
   const int row_blocks = gathered(MODE) ? int((nrows + TBM - 1) / TBM) : A.row_blocks;
-  const int items = row_blocks * A.chunks;
-  const int kb_total = A.kblocks * SEGS;
+  const int items = BATCH ? A.items_total : row_blocks * A.chunks;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -125,11 +212,13 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
     tc::mbar_init(&sm.done, 1);
     sm.abort = 0;
     tc::fence_barrier_init();
-    tc::tma_prefetch_desc(&mA0);
-    tc::tma_prefetch_desc(&mB0);
-    if (MODE == MODE_SPLIT) {
-      tc::tma_prefetch_desc(&mA1);
-      tc::tma_prefetch_desc(&mB1);
+    if (!BATCH) {
+      tc::tma_prefetch_desc(pA0);
+      tc::tma_prefetch_desc(pB0);
+      if (MODE == MODE_SPLIT) {
+        tc::tma_prefetch_desc(pA1);
+        tc::tma_prefetch_desc(pB1);
+      }
     }
   }
   if (warp == 1) {
@@ -149,17 +238,19 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       uint32_t armed_phase = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < items && ok && !A.stall; item += gridDim.x) {
-        int rb, chunk, t0, t1;
-        item_range(A, row_blocks, item, rb, chunk, t0, t1);
-        for (int ct = t0; ct < t1 && ok; ++ct) {
+        TcItem it;
+        get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it);
+        const int rb = it.rb;
+        const int kb_total = it.kblocks * SEGS;
+        for (int ct = it.t0; ct < it.t1 && ok; ++ct) {
           for (int kt = 0; kt < kb_total; ++kt) {
             if (!tc::mbar_wait(&sm.empty[stage], phase ^ 1u, abort, WAIT_LIMIT)) {
               ok = false;
               break;
             }
-            const int seg = kt / A.kblocks, kb = kt - seg * A.kblocks;
-            const CUtensorMap* ma = seg == 1 ? &mA1 : &mA0;
-            const CUtensorMap* mb = seg == 2 ? &mB1 : &mB0;
+            const int seg = kt / it.kblocks, kb = kt - seg * it.kblocks;
+            const CUtensorMap* ma = seg == 1 ? it.ma1 : it.ma0;
+            const CUtensorMap* mb = seg == 2 ? it.mb1 : it.mb0;
             tc::mbar_arrive_expect_tx(&sm.full[stage], A_BYTES + B_BYTES);
             const int kx = kb * (MODE == MODE_FP8 ? 128 : 64);
             tc::tma_load_2d(sm.a[stage], ma, &sm.full[stage], kx, rb * TBM);
@@ -176,7 +267,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       }
       if (!ok) {
         *abort = 1;
-        set_error(A.status, kErrTimeout);
+        report_timeout<BATCH>(A);
         // Let loads already issued land before the CTA exits.
         for (int s = 0; s < STAGES; ++s)
           if (armed & (1u << s)) tc::mbar_wait(&sm.full[s], (armed_phase >> s) & 1u, abort, WAIT_LIMIT);
@@ -189,9 +280,10 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       uint32_t stage = 0, phase = 0, tcount = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-        int rb, chunk, t0, t1;
-        item_range(A, row_blocks, item, rb, chunk, t0, t1);
-        for (int ct = t0; ct < t1 && ok; ++ct) {
+        TcItem it;
+        get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it);
+        const int kb_total = it.kblocks * SEGS;
+        for (int ct = it.t0; ct < it.t1 && ok; ++ct) {
           const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
           if (!tc::mbar_wait(&sm.tempty[ab], tph ^ 1u, abort, WAIT_LIMIT)) {
             ok = false;
@@ -228,7 +320,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       }
       if (!ok) {
         *abort = 1;
-        set_error(A.status, kErrTimeout);
+        report_timeout<BATCH>(A);
       }
       // Every MMA issued by this thread has completed once `done` fires.
       tc::mma_commit(&sm.done);
@@ -251,11 +343,12 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
     float ls[KL];
     int li[KL];
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
-      int rb, chunk, t0, t1;
-      item_range(A, row_blocks, item, rb, chunk, t0, t1);
-      const int64_t arow = int64_t(rb) * TBM + r;   // row of the A operand
-      const bool live = arow < nrows;
-      const int64_t grow = gathered(MODE) ? (live ? int64_t(A.rows[arow]) : -1) : A.row0 + arow;  // vertex
+      TcItem it;
+      get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it);
+      const int chunk = it.chunk;
+      const int64_t arow = int64_t(it.rb) * TBM + r;   // row of the A operand
+      const bool live = arow < it.nrows;
+      const int64_t grow = gathered(MODE) ? (live ? int64_t(A.rows[arow]) : -1) : it.row0 + arow;  // vertex
 #pragma unroll
       for (int j = 0; j < KL; ++j) {
         ls[j] = -FLT_MAX;
@@ -263,9 +356,9 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       }
       // Admission: beat the last slot and reach the floor left by chunks of
       // this row that finished earlier (s >= floor, i.e. s > the float below it).
-      const float floor_below = live ? nextafterf(key_score(A.row_floor[arow]), -INFINITY) : INFINITY;
-      const float rinv = (MODE == MODE_FP8 && live) ? A.inv_scale[grow] : 1.0f;
-      for (int ct = t0; ct < t1; ++ct) {
+      const float floor_below = live ? nextafterf(key_score(it.row_floor[arow]), -INFINITY) : INFINITY;
+      const float rinv = (MODE == MODE_FP8 && live) ? it.inv_scale[grow] : 1.0f;
+      for (int ct = it.t0; ct < it.t1; ++ct) {
         const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
         if (!tc::mbar_wait(&sm.tfull[ab], tph, abort, WAIT_LIMIT)) {
           ok = false;
@@ -281,8 +374,8 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
           // every round each lane inserts at most one admitted column with a
           // branch-free pass over its list, so the warp pays per round.
           const int64_t lbase = int64_t(ct) * TBN + cb * 32;  // B column
-          const int64_t cbase = A.col0 + lbase;                // its vertex
-          const int nvalid = int(tmin<int64_t>(A.n - lbase, 32));
+          const int64_t cbase = it.col0 + lbase;               // its vertex
+          const int nvalid = int(tmin<int64_t>(it.n - lbase, 32));
           const int64_t dself = grow - cbase;
           const int jself = (dself >= 0 && dself < 32) ? int(dself) : -1;
           const float thr = fmaxf(ls[KL - 1], floor_below);
@@ -290,7 +383,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             float s = __uint_as_float(v[j]);
-            if (MODE == MODE_FP8) s = s * rinv * __ldg(A.inv_scale + (j < nvalid ? cbase + j : 0));
+            if (MODE == MODE_FP8) s = s * rinv * __ldg(it.inv_scale + (j < nvalid ? cbase + j : 0));
             if (j == jself) s = 1.0f;
             if (j >= nvalid) s = -INFINITY;
             sm.batch[eg][j][r] = s;
@@ -330,25 +423,25 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
       }
       if (!ok) break;
       if (live) {
-        const size_t o = ((size_t(arow) * A.chunks + chunk) * EGROUPS + eg) * A.K;
+        const size_t o = ((size_t(arow) * it.chunks + chunk) * EGROUPS + eg) * it.K;
         // The K-th best as a running minimum over the first K slots (the list
         // is never indexed dynamically, so it stays in registers).
         float kth = FLT_MAX;
 #pragma unroll
         for (int j = 0; j < KL; ++j) {
-          if (j < A.K) {
-            A.part_s[o + j] = ls[j];
-            A.part_i[o + j] = li[j];
+          if (j < it.K) {
+            it.part_s[o + j] = ls[j];
+            it.part_i[o + j] = li[j];
             kth = fminf(kth, ls[j]);
           }
         }
         // This chunk's K-th best becomes a floor for the row's later chunks.
-        if (kth != -FLT_MAX) atomicMax(A.row_floor + arow, score_key(kth));
+        if (kth != -FLT_MAX) atomicMax(it.row_floor + arow, score_key(kth));
       }
     }
     if (!ok) {
       *abort = 1;
-      set_error(A.status, kErrTimeout);
+      report_timeout<BATCH>(A);
     }
   }
 
@@ -356,6 +449,21 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
   __syncthreads();
   tc::tc_fence_after();
   if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+template <int MODE, int KL, int EGROUPS>
+__global__ void __launch_bounds__(threads_of(EGROUPS), 1)
+k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+           const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs A) {
+  tc_body<MODE, KL, EGROUPS, false>(&mA0, &mA1, &mB0, &mB1, nullptr, A);
+}
+
+// Many instances in one persistent launch: the items of all instances form one
+// list that the CTAs walk; each item carries its instance's parameters.
+template <int MODE, int KL, int EGROUPS>
+__global__ void __launch_bounds__(threads_of(EGROUPS), 1)
+k1_tc_topk_batch(const __grid_constant__ TcMaps maps, TcArgs A) {
+  tc_body<MODE, KL, EGROUPS, true>(nullptr, nullptr, nullptr, nullptr, maps.m, A);
 }
 
 // Test hook: RERANK_TEST_TC_STALL set in the environment makes the kernels'
@@ -534,6 +642,63 @@ int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, 
   A.status = status;
   A.stall = stall_hook();
   launch_mode<MODE_SPLIT>(a0, a1, b0, b1, A, eg, sm_count, s);
+  return 1;
+}
+
+size_t tc_batch_inst_bytes() { return sizeof(TcInst); }
+int tc_batch_max_inst() { return kMaxBatchInst; }
+int tc_stall_hook() { return stall_hook(); }
+
+int launch_sim_tc_batch(const TcBatchInst* in, int ninst, bool fp8, void* insts_dev, void* staging, int sm_count,
+                        cudaStream_t s) {
+  if (ninst < 1 || ninst > kMaxBatchInst) return -1;
+  const int eg = tc_lists_per_chunk(in[0].dp, 1);
+  TcMaps maps;
+  TcInst* hi = static_cast<TcInst*>(staging);
+  int items = 0, kmax = 0;
+  for (int k = 0; k < ninst; ++k) {
+    const TcBatchInst& b = in[k];
+    if (tc_lists_per_chunk(b.dp, 1) != eg) return -1;
+    if (!make_map(&maps.m[k], b.xlow, b.np, b.dp, fp8)) return -1;
+    TcInst& t = hi[k];
+    t.n = b.n;
+    t.row_blocks = int(b.np / TBM);
+    t.col_tiles = int(b.np / TBN);
+    t.chunks = b.P / eg;
+    if (t.chunks < 1 || t.chunks * eg != b.P || t.chunks > t.col_tiles) return -1;
+    t.kblocks = fp8 ? b.dp / 128 : b.dp / 64;
+    t.K = b.K;
+    t.item_begin = items;
+    t.inv_scale = b.inv_scale;
+    t.row_floor = b.row_floor;
+    t.part_s = b.part_s;
+    t.part_i = b.part_i;
+    t.status = b.status;
+    items += t.row_blocks * t.chunks;
+    kmax = b.K > kmax ? b.K : kmax;
+    cudaMemsetAsync(b.row_floor, kFloorResetByte, sizeof(int) * size_t(b.n), s);
+  }
+  cudaMemcpyAsync(insts_dev, staging, sizeof(TcInst) * size_t(ninst), cudaMemcpyHostToDevice, s);
+  TcArgs A{};
+  A.insts = static_cast<const TcInst*>(insts_dev);
+  A.ninst = ninst;
+  A.items_total = items;
+  A.status = in[0].status;
+  A.stall = stall_hook();
+  const int grid = items < sm_count ? items : sm_count;
+  const size_t smem = sizeof(TcSmem) + 1024;
+  auto go = [&](auto kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    kernel<<<grid, threads_of(eg), smem, s>>>(maps, A);
+  };
+  const bool k48 = kmax <= 48;
+  if (fp8) {
+    if (eg == 2) k48 ? go(k1_tc_topk_batch<MODE_FP8, 48, 2>) : go(k1_tc_topk_batch<MODE_FP8, KLIST, 2>);
+    else k48 ? go(k1_tc_topk_batch<MODE_FP8, 48, 1>) : go(k1_tc_topk_batch<MODE_FP8, KLIST, 1>);
+  } else {
+    if (eg == 2) k48 ? go(k1_tc_topk_batch<MODE_BF16, 48, 2>) : go(k1_tc_topk_batch<MODE_BF16, KLIST, 2>);
+    else k48 ? go(k1_tc_topk_batch<MODE_BF16, 48, 1>) : go(k1_tc_topk_batch<MODE_BF16, KLIST, 1>);
+  }
   return 1;
 }
 

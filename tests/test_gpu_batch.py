@@ -53,7 +53,7 @@ def _oracle_inputs(xq, xg):
     return xq.float().cpu().numpy().astype(np.float32), xg.float().cpu().numpy().astype(np.float32)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
 def test_batch_equals_single_calls_and_oracle(lib, precision):
     inst = _small_instances()
     feats = [_features(c["w"], c["bf16"]) for c in inst]
@@ -71,6 +71,68 @@ def test_batch_equals_single_calls_and_oracle(lib, precision):
             oq, og = _oracle_inputs(xq, xg)
             ref = o.rerank(oq, og, k1=c["k1"], k2=c["k2"], layers=c["layers"], mode="sparse")
             parity.assert_ranked_equal(bi, bd, ref.s, ref.idx)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_batch_spanning_several_similarity_launches(lib, precision):
+    """More instances than one similarity launch takes (64), with feature widths
+    on both sides of the epilogue layout switch (d <= 1024 and d > 1024)."""
+    rng = np.random.default_rng(21)
+    shapes = [(int(rng.integers(1, 40)), int(rng.integers(60, 400)), [32, 64, 200, 1100][i % 4]) for i in range(70)]
+    feats = [(torch.from_numpy(rng.standard_normal((q, d)).astype(np.float32)).cuda(),
+              torch.from_numpy(rng.standard_normal((g, d)).astype(np.float32)).cuda()) for q, g, d in shapes]
+    with lib.Reranker(precision=precision) as R:
+        jobs = [dict(xq=xq, xg=xg, k1=12, k2=4, layers=2) for xq, xg in feats]
+        outs = R.run_batch(jobs)
+        torch.cuda.synchronize()
+        assert R.batch_status == [0] * len(jobs)
+        for (xq, xg), (bi, bd) in zip(feats, outs):
+            si, sd = R.run(xq, xg, 12, 4, 2)
+            torch.cuda.synchronize()
+            assert torch.equal(si, bi) and torch.equal(sd, bd)
+        for t in (0, 3, 69):
+            xq, xg = feats[t]
+            ref = o.rerank(xq.cpu().numpy(), xg.cpu().numpy(), k1=12, k2=4, layers=2, mode="sparse")
+            parity.assert_ranked_equal(outs[t][0].cpu().numpy(), outs[t][1].cpu().numpy(), ref.s, ref.idx)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_repeated_batch_replays_graph_on_new_data(lib, precision):
+    """The same buffers three times: the second call captures a CUDA graph and
+    the third replays it.  New contents in the same buffers give new results,
+    equal to single calls; other keys in between evict nothing they need."""
+    inst = _small_instances()[:5]
+    feats = [_features(c["w"], False) for c in inst]
+    rng = np.random.default_rng(8)
+    with lib.Reranker(precision=precision) as R:
+        jobs = []
+        for c, (xq, xg) in zip(inst, feats):
+            nq, ng = xq.shape[0], xg.shape[0]
+            jobs.append(dict(xq=xq, xg=xg, k1=c["k1"], k2=c["k2"], layers=c["layers"],
+                             out_idx=torch.empty((nq, ng), dtype=torch.int32, device="cuda"),
+                             out_dist=torch.empty((nq, ng), dtype=torch.float32, device="cuda")))
+        for rep in range(6):
+            if rep >= 3:
+                # fresh contents in the same buffers (the key is unchanged)
+                for j in jobs:
+                    j["xq"].copy_(torch.from_numpy(rng.standard_normal(tuple(j["xq"].shape)).astype(np.float32)))
+                    j["xg"].copy_(torch.from_numpy(rng.standard_normal(tuple(j["xg"].shape)).astype(np.float32)))
+            if rep == 4:
+                # other keys in between: two smaller batches, each run twice (captured)
+                for sub in (jobs[:2], jobs[2:4]):
+                    for _ in range(2):
+                        R.run_batch([dict(j, out_idx=None, out_dist=None) for j in sub])
+            R.run_batch(jobs)
+            torch.cuda.synchronize()
+            assert R.batch_status == [0] * len(jobs)
+            for j in jobs:
+                si, sd = R.run(j["xq"], j["xg"], j["k1"], j["k2"], j["layers"])
+                torch.cuda.synchronize()
+                assert torch.equal(si, j["out_idx"]) and torch.equal(sd, j["out_dist"]), rep
+        j = jobs[0]
+        ref = o.rerank(j["xq"].cpu().numpy(), j["xg"].cpu().numpy(), k1=j["k1"], k2=j["k2"], layers=j["layers"],
+                       mode="sparse")
+        parity.assert_ranked_equal(j["out_idx"].cpu().numpy(), j["out_dist"].cpu().numpy(), ref.s, ref.idx)
 
 
 def test_batch_host_buffers(lib):

@@ -61,6 +61,45 @@ def test_stalled_wait_returns_etimeout_and_context_recovers(built, precision):
     assert "etimeout" in r.stdout
 
 
+BATCH_STALL_CHILD = r"""
+import os, sys
+sys.path.insert(0, '.'); sys.path.insert(0, 'tests')
+import numpy as np, torch
+import parity
+from oracle import rerank_oracle as o
+from paper_2012_07620_gb300 import rerank
+rng = np.random.default_rng(4)
+xs = [(torch.from_numpy(rng.standard_normal((q, 64)).astype(np.float32)).cuda(),
+       torch.from_numpy(rng.standard_normal((g, 64)).astype(np.float32)).cuda()) for q, g in [(20, 300), (9, 150)]]
+R = rerank.Reranker(precision=sys.argv[1])
+jobs = [dict(xq=a, xg=b, k1=10, k2=4, layers=1) for a, b in xs]
+try:
+    R.run_batch(jobs)
+    print('returned without error')
+    sys.exit(1)
+except rerank.RerankError as e:
+    assert e.status == 5, e.status
+    assert R.batch_status == [5, 5], R.batch_status
+del os.environ['RERANK_TEST_TC_STALL']
+outs = R.run_batch(jobs)
+torch.cuda.synchronize()
+for (a, b), (i, d) in zip(xs, outs):
+    ref = o.rerank(a.cpu().numpy(), b.cpu().numpy(), 10, 4, 1, mode='sparse')
+    parity.assert_ranked_equal(i.cpu().numpy(), d.cpu().numpy(), ref.s, ref.idx)
+print('ok')
+"""
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_stalled_batched_launch_times_out_every_instance(built, precision):
+    """A batched similarity launch whose waits run out reports ETIMEOUT for
+    every instance it carried; the context then runs the batch correctly."""
+    env = dict(os.environ, RERANK_TEST_TC_STALL="1")
+    r = subprocess.run([sys.executable, "-c", BATCH_STALL_CHILD, precision], env=env, capture_output=True,
+                       text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0 and "ok" in r.stdout, (r.stdout[-2000:], r.stderr[-2000:])
+
+
 def test_device_reports_bad_rows(built):
     """A non-finite query row and an all-zero gallery row are found on the device
     (BF16 path): EINVAL and the first bad vertex index."""
