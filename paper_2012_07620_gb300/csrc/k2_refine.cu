@@ -372,9 +372,13 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
     eps_g += li * lmx + 1.0001 * (ri + rmx);
   }
   WarpSmem& w = sm[wib];
-  float B;
+  float B = -FLT_MAX;
   const size_t base = size_t(part_by_row ? i : f) * P * K;
-  const int cnt = merge_lists(w, part_s + base, part_i + base, P, K, n, lane, B);
+  // After a similarity stage that timed out, its lists may be unwritten (any
+  // bits, repeated columns): they are not read, and every row goes on to the
+  // exact stage as one with no candidates.
+  const bool aborted = (io.status[kStErr] & kErrTimeout) != 0;
+  const int cnt = aborted ? 0 : merge_lists(w, part_s + base, part_i + base, P, K, n, lane, B);
   if (cnt == n) B = -FLT_MAX;  // every column is a candidate
   // Fewer than k1 candidates (only after an aborted similarity stage): the
   // row goes to the next, exact stage like an uncertified one.
