@@ -9,13 +9,22 @@
 // accumulated as unsigned fixed point (2^-31 units) with shared-memory atomics;
 // integer addition is associative, so the score does not depend on the order
 // in which warps add their terms.  Zero scores (disjoint supports, the bulk of
-// the gallery) are exact.  The non-zero scores are compacted in gallery
-// order and put in order by a stable LSD radix sort on the bit-inverted score
-// (four 8-bit passes, per-warp digit histograms, __match_any_sync ranks), which
-// keeps equal scores in ascending gallery index; the zero tail follows in
-// ascending gallery index.
+// the gallery) are exact.  The non-zero scores become 64-bit sort keys
+// (bit-inverted score, gallery index): all distinct, and their ascending order
+// is the ranking (equal scores in ascending gallery index).  They are put in
+// order by one bucket pass in shared memory: the bucket of a score is its
+// binary exponent and the next 7 bits (4,096 log-spaced buckets, monotone in
+// the score), keys are scattered to their bucket's range, and each key's place
+// inside its bucket is the number of smaller keys there.  Queries with more
+// non-zeros than shared memory holds, or with a bucket too crowded for the
+// counting step (massive ties), use a stable LSD radix sort in global memory
+// (four 8-bit passes, per-warp digit histograms, __match_any_sync ranks).  The
+// zero tail follows in ascending gallery index.
 #include "common.cuh"
 #include "internal.hpp"
+
+#include <cstdio>
+#include <cstdlib>
 
 namespace rr {
 namespace {
@@ -161,8 +170,26 @@ struct RankArgs {
   float* out_dist;
   uint32_t* gscratch;   // per CTA: acc (ng) [if !acc_smem] + 4 * ng sort buffers
   int acc_smem;
+  int sort_cap;    // most non-zeros the shared-memory sort takes (SORT_CAP unless a test lowers it)
+  int bucket_cap;  // largest bucket it takes (BUCKET_CAP unless a test lowers it)
   long long* status;
 };
+
+constexpr int NB = 4096;         // score buckets of the shared-memory sort
+constexpr int BUCKET_CAP = 256;  // largest bucket the counting step takes
+static_assert(NB % RT == 0 && NB <= RW * 256, "bucket counters share the radix histogram space");
+
+// Bucket of a non-zero fixed-point score x: the position of its leading bit
+// and the 7 bits after it, so f(x) never decreases as x grows; reversed, so
+// that higher scores come first.
+__device__ __forceinline__ int score_bucket(uint32_t x) {
+  const int lz = __clz(x);
+  const uint32_t below = (x << lz) << 1;  // the bits after the leading one, left-aligned
+  const int f = ((31 - lz) << 7) | int(below >> 25);
+  return (NB - 1) - f;
+}
+
+__device__ __forceinline__ uint64_t rank_key(uint32_t x, uint32_t g) { return (uint64_t(~x) << 32) | g; }
 
 __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
   extern __shared__ uint32_t sm[];
@@ -171,15 +198,15 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
   const unsigned lt = (1u << lane) - 1u;
   const int64_t ng = A.ng;
   const int nwords = int((ng + 31) / 32);
-  uint32_t* hist = sm;                                   // RW * 256
+  uint32_t* hist = sm;                                   // RW * 256 (radix) or NB (buckets)
   int* tmp = reinterpret_cast<int*>(hist + RW * 256);    // 32
-  int* misc = tmp + 32;                                  // 32: [0] = skip flag
+  int* misc = tmp + 32;                                  // 32: [0] = skip flag, [1] = largest bucket
   uint32_t* bits = reinterpret_cast<uint32_t*>(misc + 32);  // nwords
-  uint32_t* skeys = bits + ((nwords + 3) & ~3);          // SORT_CAP
-  uint32_t* svals = skeys + SORT_CAP;                    // SORT_CAP
-  uint32_t* sacc = svals + SORT_CAP;                     // ng (when acc_smem)
+  uint64_t* kb = reinterpret_cast<uint64_t*>(bits + ((nwords + 3) & ~3));  // SORT_CAP keys, bucket order
+  uint32_t* region = reinterpret_cast<uint32_t*>(kb + SORT_CAP);  // acc (when acc_smem), later sorted keys
+  uint64_t* ks = reinterpret_cast<uint64_t*>(region);   // SORT_CAP sorted keys (the accumulator is dead by then)
   uint32_t* gbase = A.gscratch + size_t(blockIdx.x) * (5 * size_t(ng));
-  uint32_t* acc = A.acc_smem ? sacc : gbase;
+  uint32_t* acc = A.acc_smem ? region : gbase;
   uint32_t* gk0 = gbase + ng;
   uint32_t* gv0 = gk0 + ng;
   uint32_t* gk1 = gv0 + ng;
@@ -188,6 +215,8 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
 
   for (int64_t q = A.q_begin + blockIdx.x; q < A.q_end; q += gridDim.x) {
     for (int64_t g = t; g < ng; g += RT) acc[g] = 0u;
+    for (int e = t; e < NB; e += RT) hist[e] = 0u;
+    if (t == 0) misc[1] = 0;
     __syncthreads();
     const int64_t a = A.start[q];
     const int m = A.len[q];
@@ -236,9 +265,9 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
       }
     }
     __syncthreads();
-    // Non-zero bitmap and compaction, warp-cooperative: warp w owns words
-    // [w0, w1) (32 gallery entries each, lane = entry); the ballot of a word
-    // is its bitmap word, and the non-zeros go out in gallery order.
+    // Non-zero bitmap, bucket histogram and count, warp-cooperative: warp w
+    // owns words [w0, w1) (32 gallery entries each, lane = entry); the ballot
+    // of a word is its bitmap word.
     const int wpw = (nwords + RW - 1) / RW;
     const int w0 = min(nwords, w * wpw), w1 = min(nwords, w0 + wpw);
     int mine = 0;
@@ -254,6 +283,7 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
       for (int u = 0; u < 4; ++u) {
         const unsigned bal = __ballot_sync(kFull, x[u] != 0u);
         if (lane == 0 && wd + u < w1) bits[wd + u] = bal;
+        if (x[u] != 0u) atomicAdd(&hist[score_bucket(x[u])], 1u);
         mine += __popc(bal);
       }
     }
@@ -262,37 +292,101 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     off = __shfl_sync(kFull, off, 0);
     // Zeros before this warp's words: all earlier words are whole, so 32 w0 - (non-zeros before).
     const int64_t zeros_before = int64_t(w0) * 32 - off;
-    const bool small = cnt <= SORT_CAP && A.acc_smem && ng >= 2 * int64_t(cnt);
-    uint32_t* k0 = small ? skeys : gk0;
-    uint32_t* v0 = small ? svals : gv0;
-    for (int wd = w0; wd < w1; wd += 4) {
-      uint32_t bal[4], x[4];
+    bool small = cnt <= A.sort_cap;
+    if (small) {
+      // Bucket starts: exclusive scan of the histogram, four buckets per thread;
+      // the largest bucket decides whether the counting step may run.
+      uint32_t c[NB / RT];
+      int part = 0, big = 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
-        x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
+      for (int k = 0; k < NB / RT; ++k) {
+        c[k] = hist[t * (NB / RT) + k];
+        part += int(c[k]);
+        big = max(big, int(c[k]));
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if ((bal[u] >> lane) & 1u) {
-          const int pos = off + __popc(bal[u] & lt);
-          k0[pos] = ~x[u];
-          v0[pos] = uint32_t(int64_t(wd + u) * 32 + lane);
+      for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
+      if (lane == 0 && big > 0) atomicMax(&misc[1], big);
+      int base;
+      block_exscan(part, tmp, base);  // its barriers also publish misc[1]
+#pragma unroll
+      for (int k = 0; k < NB / RT; ++k) {
+        hist[t * (NB / RT) + k] = uint32_t(base);
+        base += int(c[k]);
+      }
+      small = misc[1] <= A.bucket_cap;
+      __syncthreads();
+    }
+    if (small) {
+      // Scatter every non-zero to its bucket's range (any order inside it);
+      // afterwards hist[b] is the end of bucket b.
+      for (int wd = w0; wd < w1; wd += 4) {
+        uint32_t bal[4], x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
+          x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
         }
-        off += __popc(bal[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if ((bal[u] >> lane) & 1u) {
+            const uint32_t pos = atomicAdd(&hist[score_bucket(x[u])], 1u);
+            kb[pos] = rank_key(x[u], uint32_t(int64_t(wd + u) * 32 + lane));
+          }
+        }
+      }
+      __syncthreads();
+      // Place of a key = its bucket's start + the number of smaller keys in
+      // the bucket (keys are distinct); the accumulator is no longer needed.
+      for (int p = t; p < cnt; p += RT) {
+        const uint64_t key = kb[p];
+        const int bk = score_bucket(~uint32_t(key >> 32));
+        const int b0 = bk ? int(hist[bk - 1]) : 0, b1 = int(hist[bk]);
+        int r = 0;
+        for (int j = b0; j < b1; ++j) r += kb[j] < key;
+        ks[b0 + r] = key;
+      }
+      __syncthreads();
+      const int64_t nout = tmin<int64_t>(T, cnt);
+      for (int64_t p = t; p < nout; p += RT) {
+        const uint64_t key = ks[p];
+        A.out_idx[q * T + p] = int32_t(uint32_t(key));
+        A.out_dist[q * T + p] = 1.0f - __uint2float_rn(~uint32_t(key >> 32)) * kUnfix;
+      }
+    } else {
+      // Global-memory path: non-zeros compacted in gallery order, then the
+      // stable radix sort.
+      for (int wd = w0; wd < w1; wd += 4) {
+        uint32_t bal[4], x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
+          x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if ((bal[u] >> lane) & 1u) {
+            const int pos = off + __popc(bal[u] & lt);
+            gk0[pos] = ~x[u];
+            gv0[pos] = uint32_t(int64_t(wd + u) * 32 + lane);
+          }
+          off += __popc(bal[u]);
+        }
+      }
+      __syncthreads();
+      uint32_t* k0 = gk0;
+      uint32_t* v0 = gv0;
+      uint32_t* k1 = gk1;
+      uint32_t* v1 = gv1;
+      block_radix_sort(k0, v0, k1, v1, cnt, hist, tmp, misc);
+      const int64_t nout = tmin<int64_t>(T, cnt);
+      for (int64_t p = t; p < nout; p += RT) {
+        const float s = __uint2float_rn(~k0[p]) * kUnfix;
+        A.out_idx[q * T + p] = int32_t(v0[p]);
+        A.out_dist[q * T + p] = 1.0f - s;
       }
     }
-    __syncthreads();
-    uint32_t* k1 = small ? acc : gk1;
-    uint32_t* v1 = small ? acc + cnt : gv1;
-    block_radix_sort(k0, v0, k1, v1, cnt, hist, tmp, misc);
-    // Sorted non-zeros, then the zero tail in gallery order.
-    const int64_t nout = tmin<int64_t>(T, cnt);
-    for (int64_t p = t; p < nout; p += RT) {
-      const float s = __uint2float_rn(~k0[p]) * kUnfix;
-      A.out_idx[q * T + p] = int32_t(v0[p]);
-      A.out_dist[q * T + p] = 1.0f - s;
-    }
+    // The zero tail in gallery order.
     if (T > cnt) {
       int64_t pos = cnt + zeros_before;
       for (int wd = w0; wd < w1 && pos < T; ++wd) {
@@ -313,9 +407,28 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
   }
 }
 
+// Shared memory without the accumulator: radix histograms (RW x 256 words,
+// also the NB bucket counters), scan scratch, the bitmap and the bucket-order
+// keys; the region after them holds the accumulator (when it fits) and then
+// the sorted keys, so it is never smaller than SORT_CAP keys.
 size_t rank_smem_fixed(int64_t ng) {
   const int64_t nwords = (ng + 31) / 32;
-  return sizeof(uint32_t) * (RW * 256 + 64 + ((nwords + 3) & ~int64_t(3)) + 2 * SORT_CAP);
+  return sizeof(uint32_t) * (RW * 256 + 64 + ((nwords + 3) & ~int64_t(3))) + sizeof(uint64_t) * SORT_CAP;
+}
+
+// Test hook: RERANK_TEST_RANK_CAPS="s,b" lowers the shared-memory sort's
+// limits (s non-zeros, buckets of b keys) so that tests reach the global radix
+// path on small inputs; both paths give identical lists.
+void rank_caps(int* sort_cap, int* bucket_cap) {
+  *sort_cap = SORT_CAP;
+  *bucket_cap = BUCKET_CAP;
+  if (const char* e = std::getenv("RERANK_TEST_RANK_CAPS")) {
+    int s = SORT_CAP, b = BUCKET_CAP;
+    if (std::sscanf(e, "%d,%d", &s, &b) == 2) {
+      *sort_cap = s < SORT_CAP ? s : SORT_CAP;
+      *bucket_cap = b < BUCKET_CAP ? b : BUCKET_CAP;
+    }
+  }
 }
 
 }  // namespace
@@ -323,8 +436,9 @@ size_t rank_smem_fixed(int64_t ng) {
 size_t rank_smem_bytes(int64_t ng, int threads) {
   (void)threads;
   const size_t fixed = rank_smem_fixed(ng);
-  const size_t with_acc = fixed + sizeof(uint32_t) * size_t(ng);
-  return with_acc <= 227 * 1024 ? with_acc : fixed;
+  const size_t sorted = sizeof(uint64_t) * SORT_CAP;
+  const size_t with_acc = fixed + (sizeof(uint32_t) * size_t(ng) > sorted ? sizeof(uint32_t) * size_t(ng) : sorted);
+  return with_acc <= 227 * 1024 ? with_acc : fixed + sorted;
 }
 
 int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist, long long* status,
@@ -370,7 +484,8 @@ int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out
   A.out_dist = out_dist;
   A.gscratch = b.rank_scratch;
   const size_t smem = rank_smem_bytes(ng, RT);
-  A.acc_smem = smem > rank_smem_fixed(ng);
+  A.acc_smem = smem - rank_smem_fixed(ng) >= sizeof(uint32_t) * size_t(ng);
+  rank_caps(&A.sort_cap, &A.bucket_cap);
   A.status = status;
   cudaFuncSetAttribute(k6_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const int64_t nqry = q1 - q0;

@@ -208,3 +208,35 @@ def test_overflow_retry_path():
     env = dict(os.environ, RERANK_TEST_CAP_H="60000")
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
+
+
+def test_rank_sort_paths_agree():
+    """The final ranking sorts each query's non-zero scores in shared memory by
+    buckets; queries with too many non-zeros or too crowded a bucket take the
+    global radix sort.  A test hook lowers both limits: every path gives the
+    same lists, bit for bit, and they match the oracle."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch, sys, hashlib; sys.path.insert(0, '.'); sys.path.insert(0, 'tests');"
+        "import parity; from oracle import rerank_oracle as o;"
+        "from paper_2012_07620_gb300 import rerank, synthetic;"
+        "w = synthetic.make_workload(synthetic.TINY);"
+        "xg = w.xg.copy(); xg[100:104] = xg[7];"  # copies of one gallery row (a tie group inside N(i, k2))
+        "R = rerank.Reranker(); i, d = R.run(torch.from_numpy(w.xq).cuda(), torch.from_numpy(xg).cuda(), 26, 7, 2);"
+        "torch.cuda.synchronize(); i = i.cpu().numpy(); d = d.cpu().numpy();"
+        "ref = o.rerank(w.xq, xg, 26, 7, 2, mode='sparse');"
+        "parity.assert_ranked_equal(i, d, ref.s, ref.idx);"
+        "print('digest', hashlib.sha256(i.tobytes() + d.tobytes()).hexdigest())"
+    )
+    digests = []
+    for caps in (None, "0,256", "8192,1", "8192,4"):
+        env = dict(os.environ)
+        env.pop("RERANK_TEST_RANK_CAPS", None)
+        if caps:
+            env["RERANK_TEST_RANK_CAPS"] = caps
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0 and "digest" in r.stdout, (caps, r.stderr[-2000:])
+        digests.append(r.stdout.split("digest")[-1].strip())
+    assert len(set(digests)) == 1, digests
