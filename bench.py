@@ -435,9 +435,13 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     tune_path, tuned = None, None
-    if not args.no_autotune:
+    if args.tune_file and os.path.exists(args.tune_file):
+        # Launch shapes from an earlier run's table (e.g. to profile the shapes a bench run chose).
+        tune_path = args.tune_file
+        tuned = rerank.tuning_lookup(tune_path, args.precision, nq + ng, d)
+    elif not args.no_autotune:
         # Launch shapes from the autotuner, measured on this instance before the timed region.
-        tune_path = os.path.join(tempfile.mkdtemp(), "tune.json")
+        tune_path = args.tune_file or os.path.join(tempfile.mkdtemp(), "tune.json")
         T = rerank.Reranker(device=local, precision=args.precision, autotune_path=tune_path)
         tuned = T.autotune(xq, xg, k1, k2, L)
         T.close()
@@ -556,6 +560,8 @@ def main():
                     help="length of the serving session added to the market line (0 = none)")
     ap.add_argument("--no-fp32-path", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of autotuned ones")
+    ap.add_argument("--tune-file", default=None,
+                    help="autotuner table: used as is when the file exists, else written by this run's tuning")
     args = ap.parse_args()
     world, rank, local = _dist_setup()
     if args.impl == "reference":
