@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
   const int nwords = int((ng + 31) / 32);
   uint32_t* hist = sm;                                   // RW * 256 (radix) or NB (buckets)
   int* tmp = reinterpret_cast<int*>(hist + RW * 256);    // 32
-  int* misc = tmp + 32;                                  // 32: [0] = skip flag, [1] = largest bucket
+  int* misc = tmp + 32;                                  // 32: [0] skip flag, [1] largest bucket, [2] bstar
   uint32_t* bits = reinterpret_cast<uint32_t*>(misc + 32);  // nwords
   uint64_t* kb = reinterpret_cast<uint64_t*>(bits + ((nwords + 3) & ~3));  // SORT_CAP keys, bucket order
   uint32_t* region = reinterpret_cast<uint32_t*>(kb + SORT_CAP);  // acc (when acc_smem), later sorted keys
@@ -292,34 +292,44 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     off = __shfl_sync(kFull, off, 0);
     // Zeros before this warp's words: all earlier words are whole, so 32 w0 - (non-zeros before).
     const int64_t zeros_before = int64_t(w0) * 32 - off;
+    // Only the first `cut` places are returned: the buckets up to the one
+    // holding place cut - 1 (bstar) are sorted, later ones are left out.
+    const int cut = int(tmin<int64_t>(T, cnt));
+    int bstar = -1;
     bool small = cnt <= A.sort_cap;
     if (small) {
       // Bucket starts: exclusive scan of the histogram, four buckets per thread;
-      // the largest bucket decides whether the counting step may run.
+      // the largest bucket up to bstar decides whether the counting step may run.
       uint32_t c[NB / RT];
-      int part = 0, big = 0;
+      int part = 0;
 #pragma unroll
       for (int k = 0; k < NB / RT; ++k) {
         c[k] = hist[t * (NB / RT) + k];
         part += int(c[k]);
-        big = max(big, int(c[k]));
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
-      if (lane == 0 && big > 0) atomicMax(&misc[1], big);
       int base;
-      block_exscan(part, tmp, base);  // its barriers also publish misc[1]
+      block_exscan(part, tmp, base);
 #pragma unroll
       for (int k = 0; k < NB / RT; ++k) {
         hist[t * (NB / RT) + k] = uint32_t(base);
+        if (base <= cut - 1 && cut - 1 < base + int(c[k])) misc[2] = t * (NB / RT) + k;
         base += int(c[k]);
       }
-      small = misc[1] <= A.bucket_cap;
       __syncthreads();
+      bstar = cut > 0 ? misc[2] : -1;
+      int big = 0;
+#pragma unroll
+      for (int k = 0; k < NB / RT; ++k)
+        if (t * (NB / RT) + k <= bstar) big = max(big, int(c[k]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
+      if (lane == 0 && big > 0) atomicMax(&misc[1], big);
+      __syncthreads();
+      small = misc[1] <= A.bucket_cap;
     }
     if (small) {
-      // Scatter every non-zero to its bucket's range (any order inside it);
-      // afterwards hist[b] is the end of bucket b.
+      // Scatter the non-zeros of buckets 0 .. bstar to their bucket's range
+      // (any order inside it); afterwards hist[b] is the end of bucket b.
       for (int wd = w0; wd < w1; wd += 4) {
         uint32_t bal[4], x[4];
 #pragma unroll
@@ -330,15 +340,19 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           if ((bal[u] >> lane) & 1u) {
-            const uint32_t pos = atomicAdd(&hist[score_bucket(x[u])], 1u);
-            kb[pos] = rank_key(x[u], uint32_t(int64_t(wd + u) * 32 + lane));
+            const int bk = score_bucket(x[u]);
+            if (bk <= bstar) {
+              const uint32_t pos = atomicAdd(&hist[bk], 1u);
+              kb[pos] = rank_key(x[u], uint32_t(int64_t(wd + u) * 32 + lane));
+            }
           }
         }
       }
       __syncthreads();
       // Place of a key = its bucket's start + the number of smaller keys in
       // the bucket (keys are distinct); the accumulator is no longer needed.
-      for (int p = t; p < cnt; p += RT) {
+      const int nsel = bstar >= 0 ? int(hist[bstar]) : 0;
+      for (int p = t; p < nsel; p += RT) {
         const uint64_t key = kb[p];
         const int bk = score_bucket(~uint32_t(key >> 32));
         const int b0 = bk ? int(hist[bk - 1]) : 0, b1 = int(hist[bk]);

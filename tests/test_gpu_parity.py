@@ -212,9 +212,10 @@ def test_overflow_retry_path():
 
 def test_rank_sort_paths_agree():
     """The final ranking sorts each query's non-zero scores in shared memory by
-    buckets; queries with too many non-zeros or too crowded a bucket take the
-    global radix sort.  A test hook lowers both limits: every path gives the
-    same lists, bit for bit, and they match the oracle."""
+    buckets (for a truncated list only the buckets that reach it); queries with
+    too many non-zeros or too crowded a bucket take the global radix sort.  A
+    test hook lowers both limits: every path gives the same lists, bit for bit,
+    full or truncated, and they match the oracle."""
     import os
     import subprocess
     import sys
@@ -224,11 +225,13 @@ def test_rank_sort_paths_agree():
         "from paper_2012_07620_gb300 import rerank, synthetic;"
         "w = synthetic.make_workload(synthetic.TINY);"
         "xg = w.xg.copy(); xg[100:104] = xg[7];"  # copies of one gallery row (a tie group inside N(i, k2))
-        "R = rerank.Reranker(); i, d = R.run(torch.from_numpy(w.xq).cuda(), torch.from_numpy(xg).cuda(), 26, 7, 2);"
-        "torch.cuda.synchronize(); i = i.cpu().numpy(); d = d.cpu().numpy();"
+        "R = rerank.Reranker(); tq, tg = torch.from_numpy(w.xq).cuda(), torch.from_numpy(xg).cuda();"
+        "i, d = R.run(tq, tg, 26, 7, 2); i2, d2 = R.run(tq, tg, 26, 7, 2, 37);"  # full and top-37 lists
+        "torch.cuda.synchronize(); i, d, i2, d2 = (a.cpu().numpy() for a in (i, d, i2, d2));"
         "ref = o.rerank(w.xq, xg, 26, 7, 2, mode='sparse');"
-        "parity.assert_ranked_equal(i, d, ref.s, ref.idx);"
-        "print('digest', hashlib.sha256(i.tobytes() + d.tobytes()).hexdigest())"
+        "parity.assert_ranked_equal(i, d, ref.s, ref.idx); parity.assert_ranked_equal(i2, d2, ref.s, ref.idx, 37);"
+        "assert (i2 == i[:, :37]).all() and (d2 == d[:, :37]).all();"
+        "print('digest', hashlib.sha256(i.tobytes() + d.tobytes() + i2.tobytes() + d2.tobytes()).hexdigest())"
     )
     digests = []
     for caps in (None, "0,256", "8192,1", "8192,4"):
