@@ -6,7 +6,7 @@
 //                 fill more SMs for small N, fewer keep more columns per list
 //                 and let the cross-chunk floors prune harder;
 //   prop_warps    warps per CTA of the propagation kernel (one hash table of
-//                 8 KB per warp in shared memory);
+//                 4 KB per warp in shared memory);
 //   refine_order  refine rows cluster by cluster (candidate rows shared in L1)
 //                 or in index order (no ordering pass);
 //   rescore_m     candidates kept beyond k1 (K = k1 + m): a longer list costs

@@ -252,15 +252,17 @@ __device__ bool refine_warp(WarpSmem& w, int Kc, int64_t i, int k1, float B, dou
     __syncwarp();
   };
   // Rank of each rescored candidate among [0, n): w.ord[rank] = candidate.
-  // Equal (score, index) pairs cannot occur in well-formed lists; they are
-  // ordered by position anyway, so that w.ord is always a permutation.
+  // Candidates are distinct columns, so the ranks form a permutation; the
+  // slots are filled with valid positions first, so that even a malformed
+  // list (a repeated column) can never send a later read out of range.
   auto rank_all = [&](int n) {
+    for (int c = lane; c < n; c += kWarp) w.ord[c] = c;
+    __syncwarp();
     for (int c = lane; c < n; c += kWarp) {
       const float sc = w.s[c];
       const int ic = w.idx[c];
       int r = 0;
-      for (int e = 0; e < n; ++e)
-        r += (ranks_before(w.s[e], w.idx[e], sc, ic) || (e < c && w.idx[e] == ic && w.s[e] == sc)) ? 1 : 0;
+      for (int e = 0; e < n; ++e) r += ranks_before(w.s[e], w.idx[e], sc, ic) ? 1 : 0;
       w.ord[r] = c;
     }
     __syncwarp();

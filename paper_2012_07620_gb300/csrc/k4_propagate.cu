@@ -10,9 +10,9 @@
 // exclusive scan of ub_i = sum_j len_j, an upper bound on the output row, so
 // every row can be written without a second pass.
 //
-// Rows whose distinct columns fit three quarters of a 1024-slot table (almost
+// Rows whose distinct columns fit three quarters of a 512-slot table (almost
 // all): one warp per row with a private open-addressing hash table in shared
-// memory (columns as keys), 8 KB per warp so 24 warps share an SM.  The warp
+// memory (columns as keys), 4 KB per warp so up to 48 warps share an SM.  The warp
 // walks the message list in order and adds c_j * val into the table, one
 // list at a time, so every output value is summed in message-list order and
 // the result does not depend on scheduling.  The occupied slots are
@@ -28,7 +28,7 @@
 namespace rr {
 namespace {
 
-constexpr int WSLOTS = 1024;  // hash slots per warp (8 KB: 24 warps per SM)
+constexpr int WSLOTS = 512;   // hash slots per warp (4 KB: up to 48 warps per SM)
 constexpr int WDIRECT = 4 * WSLOTS;  // ub above this goes straight to the CTA path
 constexpr int KEY_EMPTY = -1;
 constexpr int BIG_THREADS = 256;
@@ -116,7 +116,7 @@ __device__ __forceinline__ int next_pow2(int x) {
   return p;
 }
 
-constexpr int kMaxPropWarps = 24;  // 24 warps x 8 KB of tables: 192 KB, one CTA per SM
+constexpr int kMaxPropWarps = 24;  // 24 warps x 4 KB of tables: 96 KB per CTA
 
 __global__ void __launch_bounds__(kMaxPropWarps * kWarp)
 k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen, const int32_t* __restrict__ scol,
