@@ -300,31 +300,42 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     if (small) {
       // Bucket starts: exclusive scan of the histogram, four buckets per thread;
       // the largest bucket up to bstar decides whether the counting step may run.
+      const bool whole = cut == cnt;  // every non-zero is returned: bstar is the last bucket
       uint32_t c[NB / RT];
-      int part = 0;
+      int part = 0, big = 0;
 #pragma unroll
       for (int k = 0; k < NB / RT; ++k) {
         c[k] = hist[t * (NB / RT) + k];
         part += int(c[k]);
+        big = max(big, int(c[k]));
+      }
+      if (whole) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
+        if (lane == 0 && big > 0) atomicMax(&misc[1], big);
       }
       int base;
-      block_exscan(part, tmp, base);
+      block_exscan(part, tmp, base);  // its barriers also publish misc[1]
 #pragma unroll
       for (int k = 0; k < NB / RT; ++k) {
         hist[t * (NB / RT) + k] = uint32_t(base);
-        if (base <= cut - 1 && cut - 1 < base + int(c[k])) misc[2] = t * (NB / RT) + k;
+        if (!whole && base <= cut - 1 && cut - 1 < base + int(c[k])) misc[2] = t * (NB / RT) + k;
         base += int(c[k]);
       }
       __syncthreads();
-      bstar = cut > 0 ? misc[2] : -1;
-      int big = 0;
+      if (whole) {
+        bstar = cnt > 0 ? NB - 1 : -1;
+      } else {
+        bstar = misc[2];
+        big = 0;
 #pragma unroll
-      for (int k = 0; k < NB / RT; ++k)
-        if (t * (NB / RT) + k <= bstar) big = max(big, int(c[k]));
+        for (int k = 0; k < NB / RT; ++k)
+          if (t * (NB / RT) + k <= bstar) big = max(big, int(c[k]));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
-      if (lane == 0 && big > 0) atomicMax(&misc[1], big);
-      __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
+        if (lane == 0 && big > 0) atomicMax(&misc[1], big);
+        __syncthreads();
+      }
       small = misc[1] <= A.bucket_cap;
     }
     if (small) {
