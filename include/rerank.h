@@ -68,8 +68,10 @@ typedef struct {
   int rescore_m;             /* extra candidates kept per row before exact rescoring; default 16
                                 (an autotuner table entry may override it per instance size) */
   float alpha;               /* exponent of Eq. 14; default 2 */
-  int aggregator;            /* RERANK_AGG_*; default SUM (Sec. 4.1) */
-  int feature_mode;          /* RERANK_FEAT_*; default ASTAR */
+  int aggregator;            /* RERANK_AGG_*; default SUM (Sec. 4.1); MEAN divides the k2 messages'
+                                weights by k2; MAX takes their element-wise max (Eq. 13 variants) */
+  int feature_mode;          /* RERANK_FEAT_*; default ASTAR; X (dense x_i features) makes
+                                rerank_run / rerank_run_batch return EUNSUPPORTED */
   size_t hbm_budget;         /* workspace cap in bytes; 0 = no cap */
   const char* autotune_path; /* JSON tuning table to read (and to write from rerank_autotune); NULL = built-in */
   int stage_timing;          /* nonzero: record CUDA events around every stage (rerank_stage_times) */

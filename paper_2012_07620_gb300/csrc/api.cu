@@ -987,7 +987,7 @@ rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void
   if (!ctx || !xq || !xg || !out_idx || !out_dist) return RERANK_EINVAL;
   rerank_status st = rerank_check_args(nq, ng, d, dtype, k1, k2, layers, topk_out);
   if (st != RERANK_OK) return st;
-  if (ctx->cfg.aggregator == RERANK_AGG_MAX || ctx->cfg.feature_mode == RERANK_FEAT_X) return RERANK_EUNSUPPORTED;
+  if (ctx->cfg.feature_mode == RERANK_FEAT_X) return RERANK_EUNSUPPORTED;
   RR_CUDA(cudaSetDevice(ctx->device));
   const bool host_in = is_host_ptr(xq) || is_host_ptr(xg);
   const bool host_out = is_host_ptr(out_idx) || is_host_ptr(out_dist);
@@ -999,7 +999,7 @@ rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void
 
 rerank_status rerank_run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, void* stream) {
   if (!ctx || !jobs || njobs < 1) return RERANK_EINVAL;
-  if (ctx->cfg.aggregator == RERANK_AGG_MAX || ctx->cfg.feature_mode == RERANK_FEAT_X) return RERANK_EUNSUPPORTED;
+  if (ctx->cfg.feature_mode == RERANK_FEAT_X) return RERANK_EUNSUPPORTED;
   rerank_status bad = RERANK_OK;
   for (int i = 0; i < njobs; ++i) {
     rerank_job& j = jobs[i];

@@ -15,7 +15,9 @@
 // The message list of row i folds the residual term of Eq. 13 into the self
 // coefficient: entries (j, c_j) for j in N(i, k2) with c_j = e_ij^alpha (sum)
 // or e_ij^alpha / k2 (mean), and c_i gets +1; self is appended with c_i = 1
-// when it is not in N(i, k2).
+// when it is not in N(i, k2).  Max aggregator: the k2 entries (j, e_ij^alpha)
+// are combined by element-wise max, and the residual follows as a last entry
+// (i, -1): a negative coefficient means "add with weight 1".
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -130,12 +132,13 @@ __global__ void k3_edges(const int32_t* __restrict__ knn, const float* __restric
   if (i >= n) return;
   int cnt = 0;
   bool self = false;
+  const bool agg_max = aggregator == RERANK_AGG_MAX;
   for (int r = 0; r < k2; ++r) {
     const int32_t j = knn[i * k1 + r];
     const float e = score[i * k1 + r];
     float w = alpha == 2.0f ? e * e : (alpha == 0.0f ? 1.0f : powf(e, alpha));
     if (aggregator == RERANK_AGG_MEAN) w = w / float(k2);
-    if (j == i) {
+    if (j == i && !agg_max) {
       w += 1.0f;
       self = true;
     }
@@ -144,8 +147,11 @@ __global__ void k3_edges(const int32_t* __restrict__ knn, const float* __restric
     ++cnt;
   }
   if (!self) {
+    // The residual h_i of Eq. 13.  With the max aggregator it is its own last
+    // message, marked by a negative weight: added after the element-wise max
+    // of the k2 weighted neighbour rows.
     nbr[i * (k2 + 1) + cnt] = int32_t(i);
-    nbr_w[i * (k2 + 1) + cnt] = 1.0f;
+    nbr_w[i * (k2 + 1) + cnt] = agg_max ? -1.0f : 1.0f;
     ++cnt;
   }
   nbr_n[i] = cnt;

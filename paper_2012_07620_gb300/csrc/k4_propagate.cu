@@ -1,10 +1,14 @@
-// K4: one message-passing layer (Eq. 13-14, sum or mean aggregator) followed
-// by L2 normalisation (Sec. 3.3), on sparse vertex features.
+// K4: one message-passing layer (Eq. 13-14, sum, mean or max aggregator)
+// followed by L2 normalisation (Sec. 3.3), on sparse vertex features.
 //
 //   h_i <- normalise( sum_{(j, c_j) in M(i)} c_j h_j )
 //
 // where M(i) is the message list built by K3 (N(i, k2) with c_j = e_ij^alpha,
-// the residual h_i folded into c_i).  Features are stored as padded CSR: row
+// the residual h_i folded into c_i).  Max aggregator: entries with c_j >= 0
+// are combined by element-wise max (every value is >= 0, so a missing column
+// counts as 0), and the last entry, c_i = -1, adds the residual h_i on top;
+// max is exact, so the result does not depend on the order either.  Features
+// are stored as padded CSR: row
 // i occupies [start_i, start_i + len_i) of (col, val), each column at most
 // once, in no particular order (h^(0) from K3 is ascending).  start_i is an
 // exclusive scan of ub_i = sum_j len_j, an upper bound on the output row, so
@@ -64,21 +68,22 @@ __device__ __forceinline__ bool capacity_ok(const int64_t* dstart, int64_t n, in
   return true;
 }
 
-// Adds v to the entry of `col`; returns true when this call created the entry.
+// Adds v to the entry of `col` (or, with take_max, raises it to v; entries
+// start at 0 and every value is >= 0); returns true when this call created it.
 __device__ __forceinline__ bool hash_add(volatile int* keys, float* vals, int mask, int shift, int col, float v,
-                                         long long* status) {
+                                         long long* status, bool take_max = false) {
   const unsigned h = (unsigned(col) * 2654435761u) >> shift;
   for (int probe = 0; probe <= mask; ++probe) {
     const int slot = int((h + unsigned(probe)) & unsigned(mask));
     const int k = keys[slot];
     if (k == col) {
-      vals[slot] += v;
+      vals[slot] = take_max ? fmaxf(vals[slot], v) : vals[slot] + v;
       return false;
     }
     if (k == KEY_EMPTY) {
       const int old = atomicCAS(const_cast<int*>(keys) + slot, KEY_EMPTY, col);
       if (old == KEY_EMPTY || old == col) {
-        vals[slot] += v;
+        vals[slot] = take_max ? fmaxf(vals[slot], v) : vals[slot] + v;
         return old == KEY_EMPTY;
       }
     }
@@ -124,7 +129,7 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
              const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ ub,
              const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen, int32_t* __restrict__ dcol,
              float* __restrict__ dval, int64_t n, int64_t cap, int32_t* __restrict__ big_rows,
-             int32_t* __restrict__ big_count, long long* __restrict__ status) {
+             int32_t* __restrict__ big_count, long long* __restrict__ status, bool agg_max) {
   extern __shared__ int smem_i[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   volatile int* keys = smem_i + wib * WSLOTS * 2;
@@ -164,7 +169,9 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
         for (int e0 = 0; e0 < lj; e0 += kWarp) {
           const int e = e0 + lane;
           bool fresh = false;
-          if (e < lj) fresh = hash_add(keys, vals, mask, shift, scol[a + e], cj * sval[a + e], status);
+          if (e < lj)
+            fresh = hash_add(keys, vals, mask, shift, scol[a + e], fabsf(cj) * sval[a + e], status,
+                             agg_max && cj >= 0.f);
           distinct += __popc(__ballot_sync(kFull, fresh));
           __syncwarp();
           if (distinct > limit) {
@@ -213,7 +220,7 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
       }
       const float cj = __shfl_sync(kFull, qc, q);
       bool fresh = false;
-      if (col >= 0) fresh = hash_add(keys, vals, mask, shift, col, cj * val, status);
+      if (col >= 0) fresh = hash_add(keys, vals, mask, shift, col, fabsf(cj) * val, status, agg_max && cj >= 0.f);
       distinct += __popc(__ballot_sync(kFull, fresh));
       __syncwarp();  // this step's table writes are visible to the next step
       if (distinct > limit) {
@@ -277,7 +284,7 @@ k4_spmm_big(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen
             const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ big_rows,
             const int32_t* __restrict__ big_count, const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen,
             int32_t* __restrict__ dcol, float* __restrict__ dval, int64_t n, int64_t cap, float* __restrict__ dense,
-            uint32_t* __restrict__ bits, long long* __restrict__ status) {
+            uint32_t* __restrict__ bits, long long* __restrict__ status, bool agg_max) {
   __shared__ int scan_s[BIG_THREADS];
   __shared__ float red_s[BIG_THREADS];
   if (!capacity_ok(dstart, n, cap, status)) return;
@@ -298,7 +305,8 @@ k4_spmm_big(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen
       const int lj = slen[j];
       for (int e = tid; e < lj; e += BIG_THREADS) {
         const int c = scol[a + e];
-        acc[c] += cj * sval[a + e];
+        const float v = fabsf(cj) * sval[a + e];
+        acc[c] = (agg_max && cj >= 0.f) ? fmaxf(acc[c], v) : acc[c] + v;
         atomicOr(&bm[c >> 5], 1u << (c & 31));
       }
       __syncthreads();
@@ -364,7 +372,6 @@ int propagate_warp_slots() { return WSLOTS; }
 
 int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int aggregator, long long* status,
                       int sm_count, const Tuning& t, cudaStream_t s) {
-  (void)aggregator;
   const int64_t n = sh.n;
   const int k2p1 = sh.k2 + 1;
   const int T = 256;
@@ -380,12 +387,13 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
   const unsigned blocks = unsigned(tmin<int64_t>(blocks_needed, int64_t(sm_count) * (per_sm > 0 ? per_sm : 1)));
   k4_spmm_warp<<<blocks, warps * kWarp, smem, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                    b.nbr_n, k2p1, b.ub, b.start[dst], b.len[dst], b.col[dst],
-                                                   b.val[dst], n, sh.cap_h, b.big_rows, b.big_count, status);
+                                                   b.val[dst], n, sh.cap_h, b.big_rows, b.big_count, status,
+                                                   aggregator == RERANK_AGG_MAX);
   k4_spmm_big<<<sm_count, BIG_THREADS, 0, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                b.nbr_n, k2p1, b.big_rows, b.big_count, b.start[dst], b.len[dst],
                                                b.col[dst], b.val[dst], n, sh.cap_h, b.hash_keys_vals,
                                                reinterpret_cast<uint32_t*>(b.hash_keys_vals + size_t(sm_count) * n),
-                                               status);
+                                               status, aggregator == RERANK_AGG_MAX);
   return 4;
 }
 
