@@ -42,6 +42,7 @@ WORKLOADS = {
     "market": dict(spec="MARKET_SCALE", k1=26, k2=7, layers=2),
     "large50k": dict(spec="LARGE_50K", k1=26, k2=7, layers=2),
     "tiny": dict(spec="TINY", k1=26, k2=7, layers=2),
+    "market_hard": dict(spec="MARKET_HARD", k1=26, k2=7, layers=2),
     "batched64": dict(spec=None, k1=0, k2=0, layers=0),
     "serving": dict(spec=None, k1=26, k2=7, layers=2),
 }
@@ -545,6 +546,44 @@ def run_ours(args, world, rank, local):
         print(json.dumps(line))
 
 
+def run_sweep(args, world, rank, local):
+    """Synthetic accuracy sweeps (no timing): mAP and Rank-1 of the re-ranked
+    lists against the identity labels, for the layer count L (Table 2's trend)
+    or for (k1, k2) around the Eq. 15 value, beside the initial cosine ranking."""
+    import torch
+    from paper_2012_07620_gb300 import metrics, rerank, synthetic
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS[args.workload]
+    w = synthetic.make_workload(getattr(synthetic, wl["spec"]))
+    nq, ng = len(w.xq), len(w.xg)
+    xq = torch.from_numpy(w.xq).to(dev)
+    xg = torch.from_numpy(w.xg).to(dev)
+    # initial ranking: cosine of the (unit) input rows, ties to the lower index
+    s0 = w.xq.astype(np.float32) @ w.xg.astype(np.float32).T
+    base = metrics.retrieval_metrics(np.argsort(-s0, axis=1, kind="stable"), w.yq, w.yg)
+    del s0
+    k1r = metrics.k1_from_classes(nq + ng, w.spec.n_clusters)
+    if args.sweep == "layers":
+        grid = [(wl["k1"], wl["k2"], L) for L in range(0, 5)]
+    else:
+        grid = [(k1, k2, wl["layers"]) for k1 in sorted({max(2, k1r // 2), k1r, wl["k1"], 2 * k1r})
+                for k2 in (3, 5, 7, 10) if k2 <= k1]
+    rows = []
+    with rerank.Reranker(device=local, precision=args.precision) as R:
+        for k1, k2, L in grid:
+            idx, _ = R.run(xq, xg, k1, k2, L)
+            torch.cuda.synchronize()
+            m = metrics.retrieval_metrics(idx.cpu().numpy(), w.yq, w.yg)
+            rows.append({"k1": k1, "k2": k2, "layers": L, "mAP": round(m["mAP"], 4), "R1": round(m["R1"], 4)})
+    print(json.dumps({"sweep": args.sweep, "workload": wl["spec"], "precision": args.precision,
+                      "data": "synthetic", "k1_eq15": k1r,
+                      "initial_ranking": {"mAP": round(base["mAP"], 4), "R1": round(base["R1"], 4)},
+                      "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,9 +601,14 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of autotuned ones")
     ap.add_argument("--tune-file", default=None,
                     help="autotuner table: used as is when the file exists, else written by this run's tuning")
+    ap.add_argument("--sweep", default=None, choices=["layers", "k1k2"],
+                    help="synthetic accuracy sweep (mAP / Rank-1) instead of the timed run; "
+                         "use with --workload market_hard (the default set is separable)")
     args = ap.parse_args()
     world, rank, local = _dist_setup()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args, world, rank, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload == "batched64":
         run_batched(args, world, rank, local)

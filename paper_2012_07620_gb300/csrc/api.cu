@@ -163,7 +163,7 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
   b.colptr = c.take<int64_t>(size_t(n) + 1);
   b.csc_row = c.take<int32_t>(size_t(sh.cap_h));
   b.csc_val = c.take<float>(size_t(sh.cap_h));
-  b.rank_scratch = c.take<uint32_t>(size_t(sh.rank_ctas) * 5 * size_t(sh.ng));
+  b.rank_scratch = c.take<uint32_t>(size_t(sh.rank_ctas) * size_t(rank_scratch_words(sh.ng)));
   return c.used;
 }
 

@@ -308,6 +308,8 @@ int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out
                         int64_t q1, long long* status, int sm_count, const Tuning& t, cudaStream_t s);
 
 size_t rank_smem_bytes(int64_t ng, int threads);
+// 32-bit words of global scratch per ranking CTA for a gallery of ng.
+int64_t rank_scratch_words(int64_t ng);
 
 // ---- pipeline pieces shared by the single, batched and serving entry points ----
 // One pipeline instance: its shape, its buffers and its device status block.

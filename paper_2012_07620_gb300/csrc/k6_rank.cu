@@ -12,14 +12,14 @@
 // the gallery) are exact.  The non-zero scores become 64-bit sort keys
 // (bit-inverted score, gallery index): all distinct, and their ascending order
 // is the ranking (equal scores in ascending gallery index).  They are put in
-// order by one bucket pass in shared memory: the bucket of a score is its
-// binary exponent and the next 7 bits (4,096 log-spaced buckets, monotone in
-// the score), keys are scattered to their bucket's range, and each key's place
-// inside its bucket is the number of smaller keys there.  Queries with more
-// non-zeros than shared memory holds, or with a bucket too crowded for the
-// counting step (massive ties), use a stable LSD radix sort in global memory
-// (four 8-bit passes, per-warp digit histograms, __match_any_sync ranks).  The
-// zero tail follows in ascending gallery index.
+// order by one bucket pass: the bucket of a score is its binary exponent and
+// the next 7 bits (4,096 log-spaced buckets, monotone in the score), keys are
+// scattered to their bucket's range, and each key's place inside its bucket is
+// the number of smaller keys there.  The keys live in shared memory up to
+// 8,192 of them, beyond that in the CTA's global scratch.  Queries with a
+// bucket too crowded for the counting step (massive ties) use a stable LSD
+// radix sort in global memory (four 8-bit passes, per-warp digit histograms,
+// __match_any_sync ranks).  The zero tail follows in ascending gallery index.
 #include "common.cuh"
 #include "internal.hpp"
 
@@ -168,7 +168,7 @@ struct RankArgs {
   int64_t q_begin, q_end;  // queries ranked by this launch
   int32_t* out_idx;
   float* out_dist;
-  uint32_t* gscratch;   // per CTA: acc (ng) [if !acc_smem] + 4 * ng sort buffers
+  uint32_t* gscratch;   // per CTA (rank_scratch_words): acc (ng) [if !acc_smem] + 4 * ng sort buffers
   int acc_smem;
   int sort_cap;    // most non-zeros the shared-memory sort takes (SORT_CAP unless a test lowers it)
   int bucket_cap;  // largest bucket it takes (BUCKET_CAP unless a test lowers it)
@@ -191,6 +191,12 @@ __device__ __forceinline__ int score_bucket(uint32_t x) {
 
 __device__ __forceinline__ uint64_t rank_key(uint32_t x, uint32_t g) { return (uint64_t(~x) << 32) | g; }
 
+// Global scratch per ranking CTA, in 32-bit words (even, so every CTA's part
+// is 8-byte aligned): the accumulator when shared memory cannot hold it, then
+// either two 64-bit key arrays (bucket sort beyond SORT_CAP keys) or four
+// 32-bit arrays (radix sort).
+__host__ __device__ inline int64_t scratch_words(int64_t ng) { return (5 * ng + 9) & ~int64_t(1); }
+
 __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
   extern __shared__ uint32_t sm[];
   if (A.status[kStErr] & kErrOverflow) return;
@@ -205,12 +211,14 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
   uint64_t* kb = reinterpret_cast<uint64_t*>(bits + ((nwords + 3) & ~3));  // SORT_CAP keys, bucket order
   uint32_t* region = reinterpret_cast<uint32_t*>(kb + SORT_CAP);  // acc (when acc_smem), later sorted keys
   uint64_t* ks = reinterpret_cast<uint64_t*>(region);   // SORT_CAP sorted keys (the accumulator is dead by then)
-  uint32_t* gbase = A.gscratch + size_t(blockIdx.x) * (5 * size_t(ng));
+  uint32_t* gbase = A.gscratch + size_t(blockIdx.x) * size_t(scratch_words(ng));
   uint32_t* acc = A.acc_smem ? region : gbase;
   uint32_t* gk0 = gbase + ng;
   uint32_t* gv0 = gk0 + ng;
   uint32_t* gk1 = gv0 + ng;
   uint32_t* gv1 = gk1 + ng;
+  uint64_t* kbg = reinterpret_cast<uint64_t*>(gbase + ((ng + 1) & ~int64_t(1)));  // ng keys, bucket order
+  uint64_t* ksg = kbg + ng;                                                       // ng sorted keys
   const int64_t T = A.topk;
 
   for (int64_t q = A.q_begin + blockIdx.x; q < A.q_end; q += gridDim.x) {
@@ -296,8 +304,14 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     // holding place cut - 1 (bstar) are sorted, later ones are left out.
     const int cut = int(tmin<int64_t>(T, cnt));
     int bstar = -1;
-    bool small = cnt <= A.sort_cap;
-    if (small) {
+    // Keys of the bucket sort in shared memory up to sort_cap of them, else in
+    // this CTA's global scratch (L1/L2-resident); the radix sort only when a
+    // bucket is too crowded for the counting step.
+    const bool keys_smem = cnt <= A.sort_cap;
+    uint64_t* const kbx = keys_smem ? kb : kbg;
+    uint64_t* const ksx = keys_smem ? ks : ksg;
+    bool small = true;
+    {
       // Bucket starts: exclusive scan of the histogram, four buckets per thread;
       // the largest bucket up to bstar decides whether the counting step may run.
       const bool whole = cut == cnt;  // every non-zero is returned: bstar is the last bucket
@@ -354,7 +368,7 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
             const int bk = score_bucket(x[u]);
             if (bk <= bstar) {
               const uint32_t pos = atomicAdd(&hist[bk], 1u);
-              kb[pos] = rank_key(x[u], uint32_t(int64_t(wd + u) * 32 + lane));
+              kbx[pos] = rank_key(x[u], uint32_t(int64_t(wd + u) * 32 + lane));
             }
           }
         }
@@ -364,17 +378,17 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
       // the bucket (keys are distinct); the accumulator is no longer needed.
       const int nsel = bstar >= 0 ? int(hist[bstar]) : 0;
       for (int p = t; p < nsel; p += RT) {
-        const uint64_t key = kb[p];
+        const uint64_t key = kbx[p];
         const int bk = score_bucket(~uint32_t(key >> 32));
         const int b0 = bk ? int(hist[bk - 1]) : 0, b1 = int(hist[bk]);
         int r = 0;
-        for (int j = b0; j < b1; ++j) r += kb[j] < key;
-        ks[b0 + r] = key;
+        for (int j = b0; j < b1; ++j) r += kbx[j] < key;
+        ksx[b0 + r] = key;
       }
       __syncthreads();
       const int64_t nout = tmin<int64_t>(T, cnt);
       for (int64_t p = t; p < nout; p += RT) {
-        const uint64_t key = ks[p];
+        const uint64_t key = ksx[p];
         A.out_idx[q * T + p] = int32_t(uint32_t(key));
         A.out_dist[q * T + p] = 1.0f - __uint2float_rn(~uint32_t(key >> 32)) * kUnfix;
       }
@@ -441,9 +455,9 @@ size_t rank_smem_fixed(int64_t ng) {
   return sizeof(uint32_t) * (RW * 256 + 64 + ((nwords + 3) & ~int64_t(3))) + sizeof(uint64_t) * SORT_CAP;
 }
 
-// Test hook: RERANK_TEST_RANK_CAPS="s,b" lowers the shared-memory sort's
-// limits (s non-zeros, buckets of b keys) so that tests reach the global radix
-// path on small inputs; both paths give identical lists.
+// Test hook: RERANK_TEST_RANK_CAPS="s,b" lowers the bucket sort's limits (s
+// keys in shared memory, buckets of b keys) so that tests reach the global-key
+// and radix paths on small inputs; all paths give identical lists.
 void rank_caps(int* sort_cap, int* bucket_cap) {
   *sort_cap = SORT_CAP;
   *bucket_cap = BUCKET_CAP;
@@ -457,6 +471,8 @@ void rank_caps(int* sort_cap, int* bucket_cap) {
 }
 
 }  // namespace
+
+int64_t rank_scratch_words(int64_t ng) { return scratch_words(ng); }
 
 size_t rank_smem_bytes(int64_t ng, int threads) {
   (void)threads;

@@ -179,6 +179,10 @@ TINY = WorkloadSpec("tiny", 100, 900, 128, 50, 0.3, 0, None, seed=0)
 MARKET_SCALE = WorkloadSpec("market_23k_d2048", 3368, 19732, 2048, 1501, 0.35, 2000, (8, 30), seed=1)
 # A 50,000-vertex instance with 512-d features (University-1652's dimension).
 LARGE_50K = WorkloadSpec("large_50k_d512", 5000, 45000, 512, 3000, 0.35, 0, (8, 30), seed=2)
+# The Market-1501 shape with 128-d features and noise of norm 1.6: the initial
+# cosine ranking is far from perfect (mAP about 0.75), so the accuracy sweeps
+# over layers and (k1, k2) have room to show the re-ranking's effect.
+MARKET_HARD = WorkloadSpec("market_hard_d128", 3368, 19732, 128, 1501, 1.6, 2000, (8, 30), seed=5)
 # Resident gallery for the serving loop: 40,000 vectors, 2,500 clusters of 16.
 SERVING_GALLERY = WorkloadSpec("serving_gallery_40k", 0, 40000, 2048, 2500, 0.35, 0, None, seed=4)
 
