@@ -387,6 +387,8 @@ def serving_session(rerank, synthetic, dev, seconds, rate=200.0, precision="bf16
             "queue_p99_ms": float(np.percentile(qms, 99)), "requests_per_s": len(reqs) / wall,
             "queries_per_request_mean": float(nqs.mean()), "slots": info["slots"],
             "max_in_flight": info["max_in_flight"], "touched_rows_per_request": info["touched_rows"] / max(1, info["completed"]),
+            "layer_reuse": bool(info["reuse_layers"]),
+            "recomputed_layer_rows_per_request": info["recomputed_rows"] / max(1, info["completed"]),
             "slot_bytes": info["slot_bytes"], "resident_bytes": info["resident_bytes"], "gallery_load_s": t_load,
             "workload": "resident gallery 40,000 x 2048 BF16 (2,500 clusters x 16); Poisson arrivals; 1-512 "
                         "queries per request (log-uniform) from a 4,096-row pool around the gallery's identities; "

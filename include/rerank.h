@@ -222,6 +222,10 @@ typedef struct {
   int64_t touched_rows;      /* gallery rows re-derived, summed over requests */
   int64_t resident_bytes;    /* gallery data kept on the device */
   int64_t slot_bytes;        /* device memory of one slot */
+  int reuse_layers;          /* 1: the gallery's own graph and layers are kept, and a request
+                                recomputes only the layer rows whose inputs it changes */
+  int64_t recomputed_rows;   /* layer rows recomputed, summed over layers and requests (the
+                                rest were taken from the gallery's own layers) */
 } rerank_serve_info;
 rerank_status rerank_serve_info_get(const rerank_ctx* ctx, rerank_serve_info* info);
 

@@ -32,6 +32,7 @@ enum : int {
   kStTouched = 6,      // serving: gallery rows whose neighbour list a request re-derived
   kStFallbackMid = 7,  // FP8 path: rows the BF16 recheck stage could not certify
   kStNnz0 = 8,         // nnz of h^(l) at kStNnz0 + l, l <= 8
+  kStRecomputed = 17,  // serving: layer rows recomputed (not taken from the gallery's own graph)
   kStCount = 32
 };
 

@@ -296,8 +296,25 @@ int launch_scan(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
 int launch_scan32(const int32_t* in, int64_t n, int32_t* out, cudaStream_t s);
 int launch_graph(const Shape& sh, const Buffers& b, float alpha, int aggregator, int feature,
                   long long* status, cudaStream_t s);
+// Rows of a layer whose output is known elsewhere are copied instead of
+// recomputed (serving: the resident gallery's own layer rows, whose inputs a
+// request left unchanged).  Row i >= shift with changed[i] == 0 copies row
+// i - shift of the compact CSR (rstart, rlen, rcol, rval), columns + shift.
+struct LayerReuse {
+  const uint8_t* changed = nullptr;
+  const int64_t* rstart = nullptr;
+  const int32_t* rlen = nullptr;
+  const int32_t* rcol = nullptr;
+  const float* rval = nullptr;
+  int64_t shift = 0;
+};
+// Compact copy of a padded-CSR layer (rows 0 .. n-1): cstart = exclusive scan
+// of len (n + 1 entries), then the rows packed into ccol / cval.
+int launch_layer_compact(int64_t n, const int64_t* start, const int32_t* len, const int32_t* col, const float* val,
+                         const int64_t* cstart, int32_t* ccol, float* cval, cudaStream_t s);
 int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int aggregator,
-                      long long* status, int sm_count, const Tuning& t, cudaStream_t s);
+                      long long* status, int sm_count, const Tuning& t, cudaStream_t s,
+                      const LayerReuse* reuse = nullptr);
 int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s);
 int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist,
                  long long* status, int sm_count, const Tuning& t, cudaStream_t s);

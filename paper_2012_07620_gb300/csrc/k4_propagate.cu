@@ -40,7 +40,7 @@ constexpr int BIG_THREADS = 256;
 __global__ void k4_ub(const int32_t* __restrict__ nbr, const int32_t* __restrict__ nbr_n, int k2p1,
                       const int32_t* __restrict__ len, int64_t n, int32_t* __restrict__ ub,
                       int32_t* __restrict__ big_rows, int32_t* __restrict__ big_count,
-                      const long long* __restrict__ status) {
+                      const long long* __restrict__ status, LayerReuse reuse) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (status[kStErr] & kErrOverflow) {
@@ -51,8 +51,10 @@ __global__ void k4_ub(const int32_t* __restrict__ nbr, const int32_t* __restrict
   const int m = nbr_n[i];
   for (int q = 0; q < m; ++q) u += len[nbr[i * k2p1 + q]];
   if (u > n) u = n;
+  const bool copied = reuse.changed && !reuse.changed[i];
+  if (copied) u = max(u, int64_t(reuse.rlen[i - reuse.shift]));  // room for the copied row
   ub[i] = int32_t(u);
-  if (u > WDIRECT) big_rows[atomicAdd(big_count, 1)] = int32_t(i);
+  if (u > WDIRECT && !copied) big_rows[atomicAdd(big_count, 1)] = int32_t(i);
 }
 
 __device__ __forceinline__ bool capacity_ok(const int64_t* dstart, int64_t n, int64_t cap, long long* status) {
@@ -129,7 +131,7 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
              const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ ub,
              const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen, int32_t* __restrict__ dcol,
              float* __restrict__ dval, int64_t n, int64_t cap, int32_t* __restrict__ big_rows,
-             int32_t* __restrict__ big_count, long long* __restrict__ status, bool agg_max) {
+             int32_t* __restrict__ big_count, long long* __restrict__ status, bool agg_max, LayerReuse reuse) {
   extern __shared__ int smem_i[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   volatile int* keys = smem_i + wib * WSLOTS * 2;
@@ -142,6 +144,17 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
   __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
   for (int64_t i = int64_t(blockIdx.x) * nw + wib; i < n; i += int64_t(gridDim.x) * nw) {
+    if (reuse.changed && !reuse.changed[i]) {
+      // inputs unchanged: the known row, in its own column order
+      const int64_t g = i - reuse.shift, a = reuse.rstart[g], o = dstart[i];
+      const int m = reuse.rlen[g];
+      for (int p = lane; p < m; p += kWarp) {
+        dcol[o + p] = int32_t(reuse.rcol[a + p] + reuse.shift);
+        dval[o + p] = reuse.rval[a + p];
+      }
+      if (lane == 0) dlen[i] = m;
+      continue;
+    }
     const int u = ub[i];
     if (u > WDIRECT) continue;
     // Table of at least twice the bound on distinct columns, at most WSLOTS; when
@@ -366,18 +379,40 @@ __global__ void k4_row_norms(const int64_t* __restrict__ start, const int32_t* _
   if (lane == 0) rn[i] = 1.0f / sqrtf(ss);
 }
 
+__global__ void k4_compact(int64_t n, const int64_t* __restrict__ start, const int32_t* __restrict__ len,
+                           const int32_t* __restrict__ col, const float* __restrict__ val,
+                           const int64_t* __restrict__ cstart, int32_t* __restrict__ ccol, float* __restrict__ cval) {
+  const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  const int64_t a = start[i], o = cstart[i];
+  const int m = len[i];
+  for (int p = lane; p < m; p += kWarp) {
+    ccol[o + p] = col[a + p];
+    cval[o + p] = val[a + p];
+  }
+}
+
 }  // namespace
+
+int launch_layer_compact(int64_t n, const int64_t* start, const int32_t* len, const int32_t* col, const float* val,
+                         const int64_t* cstart, int32_t* ccol, float* cval, cudaStream_t s) {
+  const int T = 256;
+  k4_compact<<<unsigned((n * kWarp + T - 1) / T), T, 0, s>>>(n, start, len, col, val, cstart, ccol, cval);
+  return 1;
+}
 
 int propagate_warp_slots() { return WSLOTS; }
 
 int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int aggregator, long long* status,
-                      int sm_count, const Tuning& t, cudaStream_t s) {
+                      int sm_count, const Tuning& t, cudaStream_t s, const LayerReuse* reuse) {
   const int64_t n = sh.n;
   const int k2p1 = sh.k2 + 1;
   const int T = 256;
   cudaMemsetAsync(b.big_count, 0, sizeof(int32_t), s);
+  const LayerReuse ru = reuse ? *reuse : LayerReuse{};
   k4_ub<<<unsigned((n + T - 1) / T), T, 0, s>>>(b.nbr, b.nbr_n, k2p1, b.len[src], n, b.ub, b.big_rows, b.big_count,
-                                                 status);
+                                                 status, ru);
   launch_scan(b.ub, n, b.start[dst], s);
   const int warps = t.prop_warps < 1 ? 1 : (t.prop_warps > kMaxPropWarps ? kMaxPropWarps : t.prop_warps);
   const size_t smem = size_t(warps) * WSLOTS * 2 * sizeof(int);
@@ -388,7 +423,7 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
   k4_spmm_warp<<<blocks, warps * kWarp, smem, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                    b.nbr_n, k2p1, b.ub, b.start[dst], b.len[dst], b.col[dst],
                                                    b.val[dst], n, sh.cap_h, b.big_rows, b.big_count, status,
-                                                   aggregator == RERANK_AGG_MAX);
+                                                   aggregator == RERANK_AGG_MAX, ru);
   k4_spmm_big<<<sm_count, BIG_THREADS, 0, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                b.nbr_n, k2p1, b.big_rows, b.big_count, b.start[dst], b.len[dst],
                                                b.col[dst], b.val[dst], n, sh.cap_h, b.hash_keys_vals,

@@ -17,7 +17,12 @@
 //      merge of its resident list and its query lists (the K best of a union
 //      are the K best of the parts' K best) and it is refined like any row;
 //   4. the refinement, recheck, exact scan, graph, propagation and ranking
-//      stages, as in rerank_run, on X_u.
+//      stages, as in rerank_run, on X_u; a propagation layer recomputes only
+//      the rows whose inputs differ from the gallery's own graph (G alone,
+//      computed at load): a row whose message list and whose sources' rows of
+//      the previous layer are unchanged gets the resident row, columns shifted
+//      by Q.  Its values are those of a recomputation (each column is summed
+//      in message order, norms are exact), only their order in the row differs.
 // Every slot owns a stream and all the buffers of one request, so requests
 // on different slots overlap on the GPU and never see each other's data.
 #include <algorithm>
@@ -84,6 +89,8 @@ struct Slot {
   float* pm_s = nullptr;    // G x K: merged lists of the touched rows (by position)
   int32_t* pm_i = nullptr;
   int32_t* touched = nullptr;
+  uint8_t* chg[2] = {nullptr, nullptr};  // per union row: layer input changed (two layers in turn)
+  uint8_t* msgchg = nullptr;             // per union row: message list differs from the resident one
   int* floor_a = nullptr;
   int* floor_b = nullptr;
   void* xq_stage = nullptr;  // S x d: host queries staged here
@@ -117,6 +124,20 @@ struct Server {
   int32_t* res_knn_idx = nullptr; // G x k1 exact lists over G
   float* res_knn_score = nullptr;
   float* res_emax = nullptr;      // 4: maxima of the gallery's bounds
+  // The gallery's own graph (G alone): message lists and layers 0 .. L as
+  // compact CSR, gallery indices.  Empty when they did not fit the budget.
+  struct ResLayer {
+    int64_t* start = nullptr;
+    int32_t* len = nullptr;
+    int32_t* col = nullptr;
+    float* val = nullptr;
+  };
+  std::vector<ResLayer> res_layers;
+  int32_t* res_nbr = nullptr;
+  float* res_nbr_w = nullptr;
+  int32_t* res_nbr_n = nullptr;
+  std::vector<void*> res_extra;   // allocations of the above
+  bool reuse = false;
   std::vector<Slot> slots;
   size_t resident_bytes = 0, slot_bytes = 0;
   std::mutex mu;
@@ -127,7 +148,7 @@ struct Server {
   uint64_t next = 1;
   bool stop = false;
   int in_flight = 0, max_in_flight = 0;
-  int64_t completed = 0, touched_rows = 0;
+  int64_t completed = 0, touched_rows = 0, recomputed_rows = 0;
   std::thread worker;
 };
 
@@ -159,6 +180,9 @@ size_t slot_layout(const Server& v, Slot* sl, char* base, const Shape& shmax, in
   t.pm_s = c.take<float>(size_t(v.G) * v.K);
   t.pm_i = c.take<int32_t>(size_t(v.G) * v.K);
   t.touched = c.take<int32_t>(size_t(v.G));
+  t.chg[0] = c.take<uint8_t>(size_t(v.S + v.G));
+  t.chg[1] = c.take<uint8_t>(size_t(v.S + v.G));
+  t.msgchg = c.take<uint8_t>(size_t(v.S + v.G));
   t.floor_a = c.take<int>(size_t(v.S));
   t.floor_b = c.take<int>(size_t(v.G));
   t.xq_stage = c.take<char>(size_t(v.S) * v.d * type_size(v.dtype));
@@ -178,6 +202,55 @@ size_t slot_layout(const Server& v, Slot* sl, char* base, const Shape& shmax, in
     sl->b = b;
   }
   return ((c.used + 255) & ~size_t(255)) + ws;
+}
+
+// Layer-0 marks of a request's union rows (queries first, gallery row g at
+// union row Q + g): h0 changed when the row of A* differs from the gallery
+// graph's, msgchg when the message list (sources or weights) differs.
+__global__ void k_mark_h0(int64_t n, int64_t Q, const int64_t* __restrict__ st, const int32_t* __restrict__ ln,
+                          const int32_t* __restrict__ cl, const float* __restrict__ vl,
+                          const int64_t* __restrict__ rst, const int32_t* __restrict__ rln,
+                          const int32_t* __restrict__ rcl, const float* __restrict__ rvl,
+                          const int32_t* __restrict__ nbr, const float* __restrict__ nbr_w,
+                          const int32_t* __restrict__ nbr_n, const int32_t* __restrict__ rnbr,
+                          const float* __restrict__ rnbr_w, const int32_t* __restrict__ rnbr_n, int k2p1,
+                          uint8_t* __restrict__ h0chg, uint8_t* __restrict__ msgchg) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (i < Q) {
+    h0chg[i] = 1;
+    msgchg[i] = 1;
+    return;
+  }
+  const int64_t g = i - Q;
+  const int m = nbr_n[i];
+  bool mc = m != rnbr_n[g];
+  for (int q = 0; q < m && !mc; ++q)
+    mc = nbr[i * k2p1 + q] != rnbr[g * k2p1 + q] + Q || nbr_w[i * k2p1 + q] != rnbr_w[g * k2p1 + q];
+  const int len = ln[i];
+  bool hc = len != rln[g];
+  const int64_t a = st[i], ra = rst[g];
+  for (int p = 0; p < len && !hc; ++p) hc = cl[a + p] != rcl[ra + p] + Q || vl[a + p] != rvl[ra + p];
+  h0chg[i] = hc ? 1 : 0;
+  msgchg[i] = mc ? 1 : 0;
+}
+
+// Marks of the next layer: a row's output changes when its message list or a
+// source's row of the previous layer did.
+__global__ void k_mark_next(int64_t n, const uint8_t* __restrict__ prev, const uint8_t* __restrict__ msgchg,
+                            const int32_t* __restrict__ nbr, const int32_t* __restrict__ nbr_n, int k2p1,
+                            uint8_t* __restrict__ next, long long* __restrict__ status) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  bool c = false;
+  if (i < n) {
+    c = msgchg[i] != 0;
+    const int m = nbr_n[i];
+    for (int q = 0; q < m && !c; ++q) c = prev[nbr[i * k2p1 + q]] != 0;
+    next[i] = c ? 1 : 0;
+  }
+  const unsigned bal = __ballot_sync(kFull, c);
+  if ((threadIdx.x & 31) == 0 && bal)
+    atomicAdd(reinterpret_cast<unsigned long long*>(status + kStRecomputed), (unsigned long long)__popc(bal));
 }
 
 __global__ void k_iota(int32_t* p, int64_t n) {
@@ -421,10 +494,30 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   // 5. graph, propagation, ranking on X_u
   launch_graph(sh, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, status, s);
   RR_CUDA(cudaMemsetAsync(b.hash_keys_vals, 0, sizeof(float) * size_t(sm) * (size_t(n) + size_t((n + 31) / 32)), s));
+  const int k2p1 = v.k2 + 1;
+  const unsigned mg = unsigned((n + 255) / 256);
+  if (v.reuse) {
+    const Server::ResLayer& r0 = v.res_layers[0];
+    k_mark_h0<<<mg, 256, 0, s>>>(n, Q, b.start[2], b.len[2], b.col[2], b.val[2], r0.start, r0.len, r0.col, r0.val,
+                                 b.nbr, b.nbr_w, b.nbr_n, v.res_nbr, v.res_nbr_w, v.res_nbr_n, k2p1, sl.chg[0],
+                                 sl.msgchg);
+  }
   int src = 2;
   for (int l = 0; l < v.layers; ++l) {
     const int dst = l & 1;
-    launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, sm, sh.tune, s);
+    LayerReuse ru;
+    if (v.reuse) {
+      k_mark_next<<<mg, 256, 0, s>>>(n, sl.chg[l & 1], sl.msgchg, b.nbr, b.nbr_n, k2p1, sl.chg[(l + 1) & 1],
+                                     status);
+      const Server::ResLayer& rl = v.res_layers[size_t(l) + 1];
+      ru.changed = sl.chg[(l + 1) & 1];
+      ru.rstart = rl.start;
+      ru.rlen = rl.len;
+      ru.rcol = rl.col;
+      ru.rval = rl.val;
+      ru.shift = Q;
+    }
+    launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, sm, sh.tune, s, v.reuse ? &ru : nullptr);
     src = dst;
   }
   launch_row_norms(sh, b, src, status, s);
@@ -467,6 +560,7 @@ void worker_loop(Server* v) {
         it->second.done = true;
       }
       v->touched_rows += sl.h_status[kStTouched];
+      v->recomputed_rows += sl.h_status[kStRecomputed];
       sl.busy = false;
       --v->in_flight;
       ++v->completed;
@@ -514,6 +608,7 @@ void free_server(Server* v) {
     if (s.h_status) cudaFreeHost(s.h_status);
   }
   if (v->res_mem) cudaFree(v->res_mem);
+  for (void* p : v->res_extra) cudaFree(p);
   delete v;
 }
 
@@ -533,6 +628,101 @@ rerank_status serve_stop(rerank_ctx* ctx) {
     if (s.stream) cudaStreamSynchronize(s.stream);
   free_server(v);
   ctx->serve = nullptr;
+  return RERANK_OK;
+}
+
+// The gallery's own graph (G alone), built on slot 0's buffers at load: the
+// message lists and layers 0 .. L, kept as compact CSR.  When they do not fit
+// what the HBM budget leaves (budget_left; 0 = no budget), they are dropped
+// and requests recompute every row.  Returns a failure only for CUDA errors.
+rerank_status build_resident_graph(Server& v, cudaStream_t s0, long long* gst, size_t budget_left) {
+  rerank_ctx* ctx = v.ctx;
+  const Buffers& b = v.slots[0].b;
+  const int64_t G = v.G;
+  Shape sg;
+  sg.nq = 0;
+  sg.ng = G;
+  sg.n = G;
+  sg.np = G;
+  sg.k1 = v.k1;
+  sg.k2 = v.k2;
+  sg.layers = v.layers;
+  sg.cap_h = v.cap_h;
+  sg.tune = lookup_tuning(ctx, v.prec, G, v.d);
+  const size_t e1 = size_t(G) * size_t(v.k1), k2p1 = size_t(v.k2) + 1;
+  copy_rows(b.knn_idx, v.res_knn_idx, e1 * 4, s0);
+  copy_rows(b.knn_score, v.res_knn_score, e1 * 4, s0);
+  launch_status_reset(gst, s0);
+  launch_graph(sg, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, gst, s0);
+  RR_CUDA(cudaMemsetAsync(b.hash_keys_vals, 0,
+                          sizeof(float) * size_t(ctx->sm_count) * (size_t(G) + size_t((G + 31) / 32)), s0));
+  size_t used = 0;
+  auto alloc = [&](size_t bytes) -> void* {
+    void* p = nullptr;
+    used += (bytes + 255) & ~size_t(255);
+    if (budget_left && used > budget_left) return nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    v.res_extra.push_back(p);
+    return p;
+  };
+  auto drop = [&]() {
+    for (void* p : v.res_extra) cudaFree(p);
+    v.res_extra.clear();
+    v.res_layers.clear();
+    v.res_nbr = nullptr;
+    v.res_nbr_w = nullptr;
+    v.res_nbr_n = nullptr;
+    v.reuse = false;
+  };
+  bool ok = true;
+  v.res_nbr = static_cast<int32_t*>(alloc(size_t(G) * k2p1 * 4));
+  v.res_nbr_w = static_cast<float*>(alloc(size_t(G) * k2p1 * 4));
+  v.res_nbr_n = static_cast<int32_t*>(alloc(size_t(G) * 4));
+  ok = v.res_nbr && v.res_nbr_w && v.res_nbr_n;
+  if (ok) {
+    copy_rows(v.res_nbr, b.nbr, size_t(G) * k2p1 * 4, s0);
+    copy_rows(v.res_nbr_w, b.nbr_w, size_t(G) * k2p1 * 4, s0);
+    copy_rows(v.res_nbr_n, b.nbr_n, size_t(G) * 4, s0);
+  }
+  auto keep = [&](int layer) -> bool {
+    Server::ResLayer r;
+    r.start = static_cast<int64_t*>(alloc(size_t(G + 1) * 8));
+    r.len = static_cast<int32_t*>(alloc(size_t(G) * 4));
+    if (!r.start || !r.len) return false;
+    launch_scan(b.len[layer], G, r.start, s0);
+    copy_rows(r.len, b.len[layer], size_t(G) * 4, s0);
+    int64_t nnz = 0;
+    if (cudaMemcpyAsync(&nnz, r.start + G, sizeof(nnz), cudaMemcpyDeviceToHost, s0) != cudaSuccess ||
+        cudaStreamSynchronize(s0) != cudaSuccess)
+      return false;
+    r.col = static_cast<int32_t*>(alloc(size_t(std::max<int64_t>(nnz, 1)) * 4));
+    r.val = static_cast<float*>(alloc(size_t(std::max<int64_t>(nnz, 1)) * 4));
+    if (!r.col || !r.val) return false;
+    launch_layer_compact(G, b.start[layer], b.len[layer], b.col[layer], b.val[layer], r.start, r.col, r.val, s0);
+    v.res_layers.push_back(r);
+    return true;
+  };
+  ok = ok && keep(2);  // layer 0: the rows of A* (or A)
+  int src = 2;
+  for (int l = 0; ok && l < v.layers; ++l) {
+    const int dst = l & 1;
+    launch_propagate(sg, b, src, dst, ctx->cfg.aggregator, gst, ctx->sm_count, sg.tune, s0);
+    ok = keep(dst);
+    src = dst;
+  }
+  long long hst[kStCount];
+  RR_CUDA(cudaMemcpyAsync(hst, gst, sizeof(hst), cudaMemcpyDeviceToHost, s0));
+  RR_CUDA(cudaStreamSynchronize(s0));
+  RR_CUDA(cudaGetLastError());
+  if (!ok || hst[kStErr] != 0) {
+    drop();
+    return RERANK_OK;
+  }
+  v.reuse = true;
+  v.resident_bytes += used;
   return RERANK_OK;
 }
 
@@ -701,7 +891,17 @@ rerank_status serve_load(rerank_ctx* ctx, const void* xg, int64_t ng, int d, int
       k_iota<<<unsigned((S + 255) / 256), 256, 0, s0>>>(sl.iota, S);
     }
     if (res != RERANK_OK) break;
-    if (cudaStreamSynchronize(s0) != cudaSuccess || cudaGetLastError() != cudaSuccess) res = RERANK_ECUDA;
+    if (cudaStreamSynchronize(s0) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      res = RERANK_ECUDA;
+      break;
+    }
+    // 3. the gallery's own graph and layers, for the rows a request leaves unchanged
+    size_t left = 0;
+    if (budget) {
+      const size_t spent = v->resident_bytes + gws + v->slots.size() * v->slot_bytes;
+      left = budget > spent ? budget - spent : 1;
+    }
+    res = build_resident_graph(*v, s0, gst, left);
   } while (false);
   if (gmem) cudaFree(gmem);
   if (gst) cudaFree(gst);
@@ -776,6 +976,8 @@ rerank_status serve_info(const rerank_ctx* ctx, rerank_serve_info* info) {
   info->touched_rows = v->touched_rows;
   info->resident_bytes = int64_t(v->resident_bytes);
   info->slot_bytes = int64_t(v->slot_bytes);
+  info->reuse_layers = v->reuse ? 1 : 0;
+  info->recomputed_rows = v->recomputed_rows;
   return RERANK_OK;
 }
 

@@ -68,7 +68,7 @@ class TicketInfo(ctypes.Structure):
 class ServeInfo(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_in_flight", ctypes.c_int), ("completed", ctypes.c_int64),
                 ("touched_rows", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
-                ("slot_bytes", ctypes.c_int64)]
+                ("slot_bytes", ctypes.c_int64), ("reuse_layers", ctypes.c_int), ("recomputed_rows", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):

@@ -1,9 +1,10 @@
 """Serving: resident gallery, request loop, continuous batching.
 
 Each request is Algorithm 1 on (its queries) u (the resident gallery).  The
-tests check every served result against the FP64 oracle on that union, that
-a request's result is the same bit for bit alone and in a mix of overlapping
-requests, admission under an HBM budget, and the argument errors.
+tests check every served result against the FP64 oracle on that union (with
+the layer rows a request leaves unchanged taken from the gallery's own
+graph), that a request's result is the same bit for bit alone and in a mix of
+overlapping requests, admission under an HBM budget, and the argument errors.
 """
 import numpy as np
 import pytest
@@ -70,6 +71,9 @@ def test_served_results_match_oracle_alone_and_in_a_mix(lib, gallery, precision)
         assert info["slots"] == 4 and info["completed"] == 2 * len(qs)
         assert info["max_in_flight"] >= 2, "requests submitted together never overlapped"
         assert info["touched_rows"] > 0
+        # layer rows a request leaves unchanged come from the gallery's own graph
+        total = 2 * sum(q + gallery.xg.shape[0] for q in SIZES) * L
+        assert info["reuse_layers"] == 1 and 0 < info["recomputed_rows"] < total
         for (ai, ad), (mi, md) in zip(alone, mix):
             assert (ai == mi).all() and (ad == md).all(), "result depends on the other requests"
         for q, (ai, ad) in zip(qs, alone):
