@@ -124,10 +124,29 @@ struct TcItem {
   int32_t* part_i;
 };
 
+// Gathered launches (recheck): the row count is known on the device only, so
+// the number of column chunks is chosen there, by the host's rule (whole waves
+// of items over the grid, each chunk charged three tiles for its cold start),
+// up to the A.chunks lists per row the caller reads.
+__device__ __forceinline__ int pick_chunks(int row_blocks, int maxc, int col_tiles, int grid) {
+  int best = maxc;
+  long long best_cost = LLONG_MAX;
+  for (int c = 1; c <= maxc; ++c) {
+    const long long waves = (static_cast<long long>(row_blocks) * c + grid - 1) / grid;
+    const long long cost = waves * ((col_tiles + c - 1) / c + 3);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = c;
+    }
+  }
+  return best;
+}
+
+// chunks: column chunks of this launch (<= A.chunks, the lists per row in the output).
 template <bool BATCH>
 __device__ __forceinline__ void get_item(const TcArgs& A, const CUtensorMap* ma0, const CUtensorMap* ma1,
                                          const CUtensorMap* mb0, const CUtensorMap* mb1, const CUtensorMap* bmaps,
-                                         int row_blocks, int64_t nrows, int item, TcItem& it) {
+                                         int row_blocks, int64_t nrows, int item, TcItem& it, int chunks) {
   if (!BATCH) {
     it.ma0 = ma0;
     it.ma1 = ma1;
@@ -135,8 +154,8 @@ __device__ __forceinline__ void get_item(const TcArgs& A, const CUtensorMap* ma0
     it.mb1 = mb1;
     it.rb = item % row_blocks;
     it.chunk = item / row_blocks;
-    it.t0 = int(int64_t(it.chunk) * A.col_tiles / A.chunks);
-    it.t1 = int(int64_t(it.chunk + 1) * A.col_tiles / A.chunks);
+    it.t0 = int(int64_t(it.chunk) * A.col_tiles / chunks);
+    it.t1 = int(int64_t(it.chunk + 1) * A.col_tiles / chunks);
     it.kblocks = A.kblocks;
     it.K = A.K;
     it.chunks = A.chunks;
@@ -198,7 +217,8 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
   constexpr int SEGS = MODE == MODE_SPLIT ? 3 : 1;
   const int64_t nrows = gathered(MODE) ? int64_t(*A.count) : A.a_rows;
   const int row_blocks = gathered(MODE) ? int((nrows + TBM - 1) / TBM) : A.row_blocks;
-  const int items = BATCH ? A.items_total : row_blocks * A.chunks;
+  const int chunks = gathered(MODE) ? pick_chunks(row_blocks, A.chunks, A.col_tiles, int(gridDim.x)) : A.chunks;
+  const int items = BATCH ? A.items_total : row_blocks * chunks;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -239,7 +259,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
       bool ok = true;
       for (int item = blockIdx.x; item < items && ok && !A.stall; item += gridDim.x) {
         TcItem it;
-        get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it);
+        get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
         const int rb = it.rb;
         const int kb_total = it.kblocks * SEGS;
         for (int ct = it.t0; ct < it.t1 && ok; ++ct) {
@@ -281,7 +301,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
       bool ok = true;
       for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
         TcItem it;
-        get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it);
+        get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
         const int kb_total = it.kblocks * SEGS;
         for (int ct = it.t0; ct < it.t1 && ok; ++ct) {
           const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
@@ -344,7 +364,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
     int li[KL];
     for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
       TcItem it;
-      get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it);
+      get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
       const int chunk = it.chunk;
       const int64_t arow = int64_t(it.rb) * TBM + r;   // row of the A operand
       const bool live = arow < it.nrows;
@@ -437,6 +457,13 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
         }
         // This chunk's K-th best becomes a floor for the row's later chunks.
         if (kth != -FLT_MAX) atomicMax(it.row_floor + arow, score_key(kth));
+        // Lists of chunks this launch does not use are empty (first entry invalid).
+        if (gathered(MODE) && chunk == 0)
+          for (int c = chunks; c < it.chunks; ++c) {
+            const size_t oe = ((size_t(arow) * it.chunks + c) * EGROUPS + eg) * it.K;
+            it.part_s[oe] = -FLT_MAX;
+            it.part_i[oe] = kInvalidIdx;
+          }
       }
     }
     if (!ok) {
