@@ -94,16 +94,36 @@ __device__ __forceinline__ bool hash_add(volatile int* keys, float* vals, int ma
   return false;
 }
 
+// v^2 as a 128-bit fixed-point number, truncated to a multiple of 2^-64:
+// (hi, lo) = (floor(v^2), floor(frac(v^2) 2^64)).  For |v| < 1 (every value of
+// a normalised layer) it is m^2 2^(2e + 18) for v = m 2^(e - 23), in 64-bit
+// integer arithmetic; otherwise from the exact square in double.  Both give the
+// same bits.
+__device__ __forceinline__ void sq_fixed(float v, unsigned long long& hi, unsigned long long& lo) {
+  const uint32_t b = __float_as_uint(v) & 0x7fffffffu;
+  const int ef = int(b >> 23);
+  if (ef >= 127) {
+    const double d = double(v) * double(v);
+    const double ip = floor(d);
+    hi = static_cast<unsigned long long>(ip);
+    lo = static_cast<unsigned long long>((d - ip) * 18446744073709551616.0);  // x 2^64
+    return;
+  }
+  const unsigned long long m = ef ? ((b & 0x7fffffu) | 0x800000u) : (b & 0x7fffffu);
+  const int s = 2 * (ef ? ef - 127 : -126) + 18;
+  const unsigned long long m2 = m * m;
+  hi = 0;
+  lo = s >= 0 ? (m2 << s) : (s > -64 ? (m2 >> -s) : 0ull);
+}
+
 // Sum of squares of v[0 .. cnt) by one warp, independent of the order of the
-// values: each square is exact in double, is truncated to a multiple of
-// 2^-64, and the truncated squares are added as 128-bit integers.
+// values: each square is exact, is truncated to a multiple of 2^-64, and the
+// truncated squares are added as 128-bit integers.
 __device__ float warp_sumsq_exact(const float* v, int cnt, int lane) {
   unsigned long long hi = 0, lo = 0;
   for (int p = lane; p < cnt; p += kWarp) {
-    const double d = double(v[p]) * double(v[p]);
-    const double ip = floor(d);
-    const unsigned long long h = static_cast<unsigned long long>(ip);
-    const unsigned long long l = static_cast<unsigned long long>((d - ip) * 18446744073709551616.0);  // x 2^64
+    unsigned long long h, l;
+    sq_fixed(v[p], h, l);
     lo += l;
     hi += h + (lo < l ? 1ull : 0ull);
   }
