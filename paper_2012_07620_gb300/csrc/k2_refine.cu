@@ -98,6 +98,11 @@ __device__ double dot_fp64_raw(const RowIo& io, int64_t a, int64_t b, int lane) 
   return warp_sum(acc);
 }
 
+// Bulk prefetch of one candidate row (bytes: a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_row_l2(const float* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Two FP32 dot products of unit rows at once (independent chains for memory parallelism).
 __device__ __forceinline__ void dot2_fp32(const float* xi, const float* y0, const float* y1, int dp, int lane,
                                           float& r0, float& r1) {
@@ -224,7 +229,12 @@ __device__ bool refine_warp(WarpSmem& w, int Kc, int64_t i, int k1, float B, dou
   // FP32 scores of candidates [c0, c1) into w.s.
   auto rescore = [&](int c0, int c1) {
     if (reg) {
+      // The next group's rows are prefetched into L2 while this group is scored.
+      const uint32_t row_bytes = uint32_t(io.dp) * 4u;
+      if (lane < 4 && c0 + lane < c1) prefetch_row_l2(io.xhat + size_t(w.idx[c0 + lane]) * io.dp, row_bytes);
       for (int c = c0; c < c1; c += 4) {
+        if (lane < 4 && c + 4 + lane < c1)
+          prefetch_row_l2(io.xhat + size_t(w.idx[c + 4 + lane]) * io.dp, row_bytes);
         int j[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) j[u] = w.idx[c + u < c1 ? c + u : c];
