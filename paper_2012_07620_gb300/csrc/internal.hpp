@@ -318,11 +318,26 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
 int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s);
 int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist,
                  long long* status, int sm_count, const Tuning& t, cudaStream_t s);
+// Gallery column lists known elsewhere (serving: the gallery graph's own final
+// layer as CSC, gallery-local rows and columns, values scaled by row norms).
+// Column c >= shift of the union maps to resident column c - shift; entries of
+// gallery rows g with changed[g] != 0 are skipped (those rows are in the
+// request's own lists).
+struct RankReuse {
+  const int64_t* colptr = nullptr;
+  const int32_t* row = nullptr;
+  const float* val = nullptr;
+  const uint8_t* changed = nullptr;
+  int64_t shift = 0;
+};
 // The same in two parts: the gallery's column lists once, then queries [q0, q1)
-// (out_idx / out_dist still address the whole nq x topk output).
-int launch_rank_prep(const Shape& sh, const Buffers& b, int src, long long* status, cudaStream_t s);
+// (out_idx / out_dist still address the whole nq x topk output).  rows_sel
+// (per union row, nullable): only gallery rows with rows_sel[r] != 0 enter the lists.
+int launch_rank_prep(const Shape& sh, const Buffers& b, int src, long long* status, cudaStream_t s,
+                     const uint8_t* rows_sel = nullptr);
 int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist, int64_t q0,
-                        int64_t q1, long long* status, int sm_count, const Tuning& t, cudaStream_t s);
+                        int64_t q1, long long* status, int sm_count, const Tuning& t, cudaStream_t s,
+                        const RankReuse* reuse = nullptr);
 
 size_t rank_smem_bytes(int64_t ng, int threads);
 // 32-bit words of global scratch per ranking CTA for a gallery of ng.

@@ -37,10 +37,10 @@ constexpr float kUnfix = 4.656612873077393e-10f;  // 2^-31
 
 __global__ void k5_count(const int64_t* __restrict__ start, const int32_t* __restrict__ len,
                          const int32_t* __restrict__ col, int64_t nq, int64_t n, int32_t* __restrict__ colcnt,
-                         const long long* __restrict__ status) {
+                         const long long* __restrict__ status, const uint8_t* __restrict__ sel) {
   const int64_t r = nq + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (r >= n || (status[kStErr] & kErrOverflow)) return;
+  if (r >= n || (status[kStErr] & kErrOverflow) || (sel && !sel[r])) return;
   const int64_t a = start[r];
   const int m = len[r];
   for (int p = lane; p < m; p += kWarp) atomicAdd(&colcnt[col[a + p]], 1);
@@ -50,10 +50,10 @@ __global__ void k5_fill(const int64_t* __restrict__ start, const int32_t* __rest
                         const int32_t* __restrict__ col, const float* __restrict__ val, const float* __restrict__ rn,
                         int64_t nq, int64_t n, const int64_t* __restrict__ colptr, int32_t* __restrict__ fill,
                         int32_t* __restrict__ csc_row, float* __restrict__ csc_val,
-                        const long long* __restrict__ status) {
+                        const long long* __restrict__ status, const uint8_t* __restrict__ sel) {
   const int64_t r = nq + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (r >= n || (status[kStErr] & kErrOverflow)) return;
+  if (r >= n || (status[kStErr] & kErrOverflow) || (sel && !sel[r])) return;
   const int64_t a = start[r];
   const int m = len[r];
   const float s = rn[r];
@@ -170,6 +170,7 @@ struct RankArgs {
   float* out_dist;
   uint32_t* gscratch;   // per CTA (rank_scratch_words): acc (ng) [if !acc_smem] + 4 * ng sort buffers
   int acc_smem;
+  RankReuse reuse;  // resident gallery lists (colptr null: none)
   int sort_cap;    // most non-zeros the shared-memory sort takes (SORT_CAP unless a test lowers it)
   int bucket_cap;  // largest bucket it takes (BUCKET_CAP unless a test lowers it)
   long long* status;
@@ -270,6 +271,30 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
         v = vn;
         p0 = n0;
         p1 = n1;
+      }
+    }
+    if (A.reuse.colptr) {
+      // The same over the resident lists of the columns of gallery vertices,
+      // for the gallery rows the request left unchanged.
+      const RankReuse& R = A.reuse;
+      for (int e = w; e < m; e += RW) {
+        const int64_t c = A.col[a + e] - R.shift;
+        if (c < 0) continue;
+        const float v = A.val[a + e] * rq;
+        const int64_t p1 = R.colptr[c + 1];
+        for (int64_t p = R.colptr[c] + lane; p < p1; p += 4 * kWarp) {
+          int r[4];
+          float x[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t pp = p + u * kWarp;
+            r[u] = pp < p1 ? R.row[pp] : -1;
+            x[u] = pp < p1 ? R.val[pp] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (r[u] >= 0 && !R.changed[r[u]]) atomicAdd(&acc[r[u]], __float2uint_rn(v * x[u] * kFix));
+        }
       }
     }
     __syncthreads();
@@ -489,21 +514,24 @@ int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, fl
   return nl;
 }
 
-int launch_rank_prep(const Shape& sh, const Buffers& b, int src, long long* status, cudaStream_t s) {
+int launch_rank_prep(const Shape& sh, const Buffers& b, int src, long long* status, cudaStream_t s,
+                     const uint8_t* rows_sel) {
   const int64_t n = sh.n, nq = sh.nq, ng = sh.ng;
   const int T = 256;
   cudaMemsetAsync(b.colcnt, 0, sizeof(int32_t) * (n + 1), s);
   k5_count<<<unsigned((ng * kWarp + T - 1) / T), T, 0, s>>>(b.start[src], b.len[src], b.col[src], nq, n, b.colcnt,
-                                                            status);
+                                                            status, rows_sel);
   launch_scan(b.colcnt, n, b.colptr, s);
   cudaMemsetAsync(b.colcnt, 0, sizeof(int32_t) * (n + 1), s);
   k5_fill<<<unsigned((ng * kWarp + T - 1) / T), T, 0, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.rnorm,
-                                                           nq, n, b.colptr, b.colcnt, b.csc_row, b.csc_val, status);
+                                                           nq, n, b.colptr, b.colcnt, b.csc_row, b.csc_val, status,
+                                                           rows_sel);
   return 3;
 }
 
 int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist, int64_t q0,
-                        int64_t q1, long long* status, int sm_count, const Tuning& tune, cudaStream_t s) {
+                        int64_t q1, long long* status, int sm_count, const Tuning& tune, cudaStream_t s,
+                        const RankReuse* reuse) {
   (void)tune;
   (void)sm_count;
   const int64_t nq = sh.nq, ng = sh.ng;
@@ -524,6 +552,7 @@ int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out
   A.out_idx = out_idx;
   A.out_dist = out_dist;
   A.gscratch = b.rank_scratch;
+  A.reuse = reuse ? *reuse : RankReuse{};
   const size_t smem = rank_smem_bytes(ng, RT);
   A.acc_smem = smem - rank_smem_fixed(ng) >= sizeof(uint32_t) * size_t(ng);
   rank_caps(&A.sort_cap, &A.bucket_cap);

@@ -133,6 +133,9 @@ struct Server {
     float* val = nullptr;
   };
   std::vector<ResLayer> res_layers;
+  int64_t* res_colptr = nullptr;  // the last layer as CSC (row norms applied): gallery columns
+  int32_t* res_csc_row = nullptr;
+  float* res_csc_val = nullptr;
   int32_t* res_nbr = nullptr;
   float* res_nbr_w = nullptr;
   int32_t* res_nbr_n = nullptr;
@@ -523,7 +526,21 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   launch_row_norms(sh, b, src, status, s);
   int32_t* oi = host_out ? b.out_idx : rq.out_idx;
   float* od = host_out ? b.out_dist : rq.out_dist;
-  launch_rank(sh, b, src, oi, od, status, sm, sh.tune, s);
+  if (v.reuse) {
+    // the gallery rows of the last layer that changed get new column lists;
+    // the others' entries come from the gallery graph's own lists
+    const uint8_t* last = sl.chg[v.layers & 1];
+    RankReuse rr;
+    rr.colptr = v.res_colptr;
+    rr.row = v.res_csc_row;
+    rr.val = v.res_csc_val;
+    rr.changed = last + Q;
+    rr.shift = Q;
+    launch_rank_prep(sh, b, src, status, s, last);
+    launch_rank_queries(sh, b, src, oi, od, 0, Q, status, sm, sh.tune, s, &rr);
+  } else {
+    launch_rank(sh, b, src, oi, od, status, sm, sh.tune, s);
+  }
   if (host_out) {
     const size_t cnt = size_t(Q) * size_t(topk);
     RR_CUDA(cudaMemcpyAsync(rq.out_idx, b.out_idx, cnt * 4, cudaMemcpyDeviceToHost, s));
@@ -675,6 +692,9 @@ rerank_status build_resident_graph(Server& v, cudaStream_t s0, long long* gst, s
     v.res_nbr = nullptr;
     v.res_nbr_w = nullptr;
     v.res_nbr_n = nullptr;
+    v.res_colptr = nullptr;
+    v.res_csc_row = nullptr;
+    v.res_csc_val = nullptr;
     v.reuse = false;
   };
   bool ok = true;
@@ -712,6 +732,28 @@ rerank_status build_resident_graph(Server& v, cudaStream_t s0, long long* gst, s
     launch_propagate(sg, b, src, dst, ctx->cfg.aggregator, gst, ctx->sm_count, sg.tune, s0);
     ok = keep(dst);
     src = dst;
+  }
+  if (ok) {
+    // the last layer's column lists, as the ranking uses them
+    launch_row_norms(sg, b, src, gst, s0);
+    launch_rank_prep(sg, b, src, gst, s0);
+    int64_t nnz = 0;
+    v.res_colptr = static_cast<int64_t*>(alloc(size_t(G + 1) * 8));
+    ok = v.res_colptr != nullptr;
+    if (ok) {
+      copy_rows(v.res_colptr, b.colptr, size_t(G + 1) * 8, s0);
+      ok = cudaMemcpyAsync(&nnz, b.colptr + G, sizeof(nnz), cudaMemcpyDeviceToHost, s0) == cudaSuccess &&
+           cudaStreamSynchronize(s0) == cudaSuccess;
+    }
+    if (ok) {
+      v.res_csc_row = static_cast<int32_t*>(alloc(size_t(std::max<int64_t>(nnz, 1)) * 4));
+      v.res_csc_val = static_cast<float*>(alloc(size_t(std::max<int64_t>(nnz, 1)) * 4));
+      ok = v.res_csc_row && v.res_csc_val;
+    }
+    if (ok) {
+      copy_rows(v.res_csc_row, b.csc_row, size_t(nnz) * 4, s0);
+      copy_rows(v.res_csc_val, b.csc_val, size_t(nnz) * 4, s0);
+    }
   }
   long long hst[kStCount];
   RR_CUDA(cudaMemcpyAsync(hst, gst, sizeof(hst), cudaMemcpyDeviceToHost, s0));
