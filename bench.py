@@ -203,7 +203,7 @@ def _config(args, w):
 # DRAM bytes (read + write) of one similarity launch, from `ncu --set full` captures
 # (profiles/k1_tc_topk_bf16_market_23k_d2048.md); None where no capture of the
 # current kernel exists.
-SIM_TRAFFIC_BYTES = {("bf16", "market"): 353.2e6}
+SIM_TRAFFIC_BYTES = {("bf16", "market"): 389.4e6}
 
 
 def _roofline(precision, sim_ms, n, d, workload):
