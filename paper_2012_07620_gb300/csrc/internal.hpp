@@ -315,7 +315,9 @@ int launch_layer_compact(int64_t n, const int64_t* start, const int32_t* len, co
 int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int aggregator,
                       long long* status, int sm_count, const Tuning& t, cudaStream_t s,
                       const LayerReuse* reuse = nullptr);
-int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s);
+// rows_sel (nullable): only rows with rows_sel[i] != 0 get their norm.
+int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s,
+                     const uint8_t* rows_sel = nullptr);
 int launch_rank(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist,
                  long long* status, int sm_count, const Tuning& t, cudaStream_t s);
 // Gallery column lists known elsewhere (serving: the gallery graph's own final

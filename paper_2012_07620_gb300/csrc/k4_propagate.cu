@@ -388,11 +388,11 @@ k4_spmm_big(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen
 
 __global__ void k4_row_norms(const int64_t* __restrict__ start, const int32_t* __restrict__ len,
                              const float* __restrict__ val, int64_t n, float* __restrict__ rn,
-                             const long long* __restrict__ status) {
+                             const long long* __restrict__ status, const uint8_t* __restrict__ sel) {
   const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   // After an overflowing layer the row lengths of its output were never written.
-  if (i >= n || (status[kStErr] & kErrOverflow)) return;
+  if (i >= n || (status[kStErr] & kErrOverflow) || (sel && !sel[i])) return;
   const int64_t a = start[i];
   const int m = len[i];
   const float ss = warp_sumsq_exact(val + a, m, lane);
@@ -452,10 +452,11 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
   return 4;
 }
 
-int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s) {
+int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s,
+                     const uint8_t* rows_sel) {
   const int T = 256;
   k4_row_norms<<<unsigned((sh.n * kWarp + T - 1) / T), T, 0, s>>>(b.start[src], b.len[src], b.val[src], sh.n,
-                                                                   b.rnorm, status);
+                                                                   b.rnorm, status, rows_sel);
   return 1;
 }
 

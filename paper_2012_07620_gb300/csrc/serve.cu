@@ -523,7 +523,9 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
     launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, sm, sh.tune, s, v.reuse ? &ru : nullptr);
     src = dst;
   }
-  launch_row_norms(sh, b, src, status, s);
+  // With the gallery graph kept, only the rows whose last layer changed (the
+  // queries among them) need their norm: the others' are in the resident lists.
+  launch_row_norms(sh, b, src, status, s, v.reuse ? sl.chg[v.layers & 1] : nullptr);
   int32_t* oi = host_out ? b.out_idx : rq.out_idx;
   float* od = host_out ? b.out_dist : rq.out_dist;
   if (v.reuse) {
