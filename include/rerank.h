@@ -91,6 +91,11 @@ rerank_status rerank_destroy(rerank_ctx* ctx);
 /* Static text for a status code. */
 const char* rerank_strerror(rerank_status status);
 
+/* The CUDA call and CUDA error text behind the calling thread's last ECUDA or
+ * ENOMEM status ("" when there was none).  The string belongs to the library
+ * and stays valid until the thread's next failing call. */
+const char* rerank_last_cuda_error(void);
+
 /* Host-only validation of the size arguments of rerank_run (no GPU needed):
  * EINVAL unless nq >= 1, ng >= 1, d >= 1, dtype valid, 1 <= k2 <= k1 <= nq+ng,
  * layers >= 0 and 0 <= topk_out <= ng. */

@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 
+#include <cuda.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
@@ -167,9 +168,21 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
   return c.used;
 }
 
+void free_graph(BatchGraph* g);
+
+// Cached batch graphs hold copy and memset nodes on the workspace and on the
+// pinned status block; a new allocation can come back at the same address
+// (so a key of pointers would still match), so every graph goes with the old one.
+void drop_graphs(rerank_ctx* ctx) {
+  for (BatchGraph* g : ctx->graphs) free_graph(g);
+  ctx->graphs.clear();
+  ctx->graph_seen.clear();
+}
+
 rerank_status ensure_workspace(rerank_ctx* ctx, size_t bytes) {
   if (ctx->cfg.hbm_budget && bytes > ctx->cfg.hbm_budget) return RERANK_EBUDGET;
   if (bytes <= ctx->ws_bytes) return RERANK_OK;
+  drop_graphs(ctx);
   if (ctx->ws) {
     cudaFree(ctx->ws);
     ctx->ws = nullptr;
@@ -547,6 +560,7 @@ rerank_status ensure_streams(rerank_ctx* ctx) {
 
 rerank_status ensure_host_status(rerank_ctx* ctx, size_t count) {
   if (count <= ctx->h_batch_count) return RERANK_OK;
+  drop_graphs(ctx);
   if (ctx->h_batch) cudaFreeHost(ctx->h_batch);
   ctx->h_batch = nullptr;
   ctx->h_batch_count = 0;
@@ -573,6 +587,25 @@ bool is_pageable(const void* p) {
     return true;
   }
   return a.type == cudaMemoryTypeUnregistered;
+}
+
+using PtrAttrFn = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+
+// Process-wide unique id of the allocation holding p, 0 when the driver does
+// not know p.  Graph keys carry it beside each pointer, so a buffer freed and
+// allocated again at the same address does not match a graph of the old one.
+uint64_t buffer_id(const void* p) {
+  static const PtrAttrFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<PtrAttrFn>(f);
+  }();
+  unsigned long long id = 0;
+  if (!fn || !p || fn(&id, CU_POINTER_ATTRIBUTE_BUFFER_ID, reinterpret_cast<CUdeviceptr>(p)) != CUDA_SUCCESS) return 0;
+  return id;
 }
 
 // Every field of a planned instance: together with the job's pointers and
@@ -798,10 +831,12 @@ rerank_status run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, cudaStream
   }
   if (graphable) {
     std::vector<int64_t> key;
-    key.reserve(size_t(njobs) * 40 + 8);
+    key.reserve(size_t(njobs) * 44 + 10);
     key.push_back(int64_t(reinterpret_cast<uintptr_t>(ctx->ws)));
+    key.push_back(int64_t(buffer_id(ctx->ws)));
     key.push_back(int64_t(total));
     key.push_back(int64_t(reinterpret_cast<uintptr_t>(ctx->h_batch)));
+    key.push_back(int64_t(buffer_id(ctx->h_batch)));
     key.push_back(tc_stall_hook());
     for (int i = 0; i < njobs; ++i) {
       const rerank_job& jb = jobs[i];
@@ -809,6 +844,8 @@ rerank_status run_batch(rerank_ctx* ctx, rerank_job* jobs, int njobs, cudaStream
       key.push_back(int64_t(reinterpret_cast<uintptr_t>(jb.xg)));
       key.push_back(int64_t(reinterpret_cast<uintptr_t>(jb.out_idx)));
       key.push_back(int64_t(reinterpret_cast<uintptr_t>(jb.out_dist)));
+      for (const void* p : {jb.xq, jb.xg, static_cast<const void*>(jb.out_idx), static_cast<const void*>(jb.out_dist)})
+        key.push_back(int64_t(buffer_id(p)));
       key.push_back(int64_t(off[size_t(i)]));
       shape_key(runs[size_t(i)].sh, key);
     }
@@ -900,6 +937,8 @@ void rerank_config_init(rerank_config* cfg) {
   cfg->autotune_path = nullptr;
   cfg->stage_timing = 0;
 }
+
+const char* rerank_last_cuda_error(void) { return rr::last_cuda_error_text(); }
 
 const char* rerank_strerror(rerank_status s) {
   switch (s) {

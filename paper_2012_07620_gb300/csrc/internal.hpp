@@ -197,7 +197,9 @@ struct rerank_ctx {
   size_t h_batch_count = 0;
   void* h_stage = nullptr;  // pinned: instance tables of batched similarity launches
   size_t h_stage_bytes = 0;
-  // batched calls replayed as CUDA graphs (least recently used evicted)
+  // batched calls replayed as CUDA graphs (least recently used evicted); all
+  // dropped when the workspace or the pinned status block is reallocated,
+  // since their copy and memset nodes name those allocations
   std::vector<rr::BatchGraph*> graphs;
   uint64_t graph_clock = 0;
   std::vector<uint64_t> graph_seen;  // hashes of recent keys not yet captured

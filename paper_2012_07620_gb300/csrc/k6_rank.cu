@@ -450,21 +450,36 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
         A.out_dist[q * T + p] = 1.0f - s;
       }
     }
-    // The zero tail in gallery order.
+    // The zero tail in gallery order.  Its distances are all 1: plain
+    // block-wide stores, 16 bytes each once aligned.  Its indices: warp w
+    // writes the zeros of its words, four words per step.
     if (T > cnt) {
+      float* dq = A.out_dist + q * T;
+      const int64_t head = tmin<int64_t>((4 - int((reinterpret_cast<uintptr_t>(dq + cnt) >> 2) & 3)) & 3, T - cnt);
+      if (t < head) dq[cnt + t] = 1.0f;
+      const int64_t p0 = cnt + head, nv = (T - p0) >> 2;
+      float4* dv = reinterpret_cast<float4*>(dq + p0);
+      for (int64_t v = t; v < nv; v += RT) dv[v] = make_float4(1.f, 1.f, 1.f, 1.f);
+      for (int64_t p = p0 + 4 * nv + t; p < T; p += RT) dq[p] = 1.0f;
+      int32_t* iq = A.out_idx + q * T;
       int64_t pos = cnt + zeros_before;
-      for (int wd = w0; wd < w1 && pos < T; ++wd) {
-        const int valid = int(tmin<int64_t>(32, ng - int64_t(wd) * 32));
-        const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
-        const uint32_t zb = ~bits[wd] & vm;
-        if ((zb >> lane) & 1u) {
-          const int64_t p = pos + __popc(zb & lt);
-          if (p < T) {
-            A.out_idx[q * T + p] = int32_t(int64_t(wd) * 32 + lane);
-            A.out_dist[q * T + p] = 1.0f;
-          }
+      for (int wd0 = w0; wd0 < w1 && pos < T; wd0 += 4) {
+        uint32_t zb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int wd = wd0 + u;
+          const int valid = wd < w1 ? int(tmin<int64_t>(32, ng - int64_t(wd) * 32)) : 0;
+          const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
+          zb[u] = wd < w1 ? (~bits[wd] & vm) : 0u;
         }
-        pos += __popc(zb);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if ((zb[u] >> lane) & 1u) {
+            const int64_t p = pos + __popc(zb[u] & lt);
+            if (p < T) iq[p] = int32_t(int64_t(wd0 + u) * 32 + lane);
+          }
+          pos += __popc(zb[u]);
+        }
       }
     }
     __syncthreads();

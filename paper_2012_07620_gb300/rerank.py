@@ -79,7 +79,12 @@ class Tuning(ctypes.Structure):
 class RerankError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} ({strerror(status)})")
+        text = f"{where}: {STATUS_NAMES.get(status, status)} ({strerror(status)})"
+        if status in (2, 4):  # ENOMEM, ECUDA: name the failing CUDA call
+            cuda = load_library().rerank_last_cuda_error().decode()
+            if cuda:
+                text += f" [{cuda}]"
+        super().__init__(text)
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -89,6 +94,7 @@ _SIGS = {
     "rerank_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(RerankConfig)]),
     "rerank_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "rerank_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "rerank_last_cuda_error": (ctypes.c_char_p, []),
     "rerank_check_args": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
     "rerank_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,

@@ -135,6 +135,41 @@ def test_repeated_batch_replays_graph_on_new_data(lib, precision):
         parity.assert_ranked_equal(j["out_idx"].cpu().numpy(), j["out_dist"].cpu().numpy(), ref.s, ref.idx)
 
 
+def test_graph_cache_survives_workspace_regrowth(lib):
+    """A captured batch graph names the workspace allocation.  A larger single
+    call in between replaces the workspace (the new block may start at the same
+    address); the next identical batch call must not replay the old graph, and
+    its results stay equal to single calls."""
+    inst = _small_instances()[:3]
+    feats = [_features(c["w"], False) for c in inst]
+    big = synthetic.make_workload(synthetic.WorkloadSpec("grow", 1500, 10500, 1024, 600, 0.35, 0, None, seed=77))
+    bq, bg = torch.from_numpy(big.xq).cuda(), torch.from_numpy(big.xg).cuda()
+    with lib.Reranker(precision="bf16") as R:
+        jobs = []
+        for c, (xq, xg) in zip(inst, feats):
+            nq, ng = xq.shape[0], xg.shape[0]
+            jobs.append(dict(xq=xq, xg=xg, k1=c["k1"], k2=c["k2"], layers=c["layers"],
+                             out_idx=torch.empty((nq, ng), dtype=torch.int32, device="cuda"),
+                             out_dist=torch.empty((nq, ng), dtype=torch.float32, device="cuda")))
+        for _ in range(3):  # direct, captured, replayed
+            R.run_batch(jobs)
+        torch.cuda.synchronize()
+        ws0 = R.last_info()["workspace_bytes"]
+        R.run(bq, bg, 26, 7, 2, topk_out=10)
+        torch.cuda.synchronize()
+        assert R.last_info()["workspace_bytes"] > ws0, "the single call did not grow the workspace"
+        for _ in range(3):
+            for j in jobs:
+                j["out_idx"].fill_(-1)
+            R.run_batch(jobs)
+            torch.cuda.synchronize()
+            assert R.batch_status == [0] * len(jobs)
+            for j in jobs:
+                si, sd = R.run(j["xq"], j["xg"], j["k1"], j["k2"], j["layers"])
+                torch.cuda.synchronize()
+                assert torch.equal(si, j["out_idx"]) and torch.equal(sd, j["out_dist"])
+
+
 def test_batch_host_buffers(lib):
     """NumPy (host) inputs and outputs in a batch are staged by the library."""
     inst = _small_instances()[:3]
