@@ -969,13 +969,16 @@ rerank_status rerank_create(rerank_ctx** out, const rerank_config* cfg) {
   *out = nullptr;
   if (!valid_enum(cfg)) return RERANK_EINVAL;
   int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+  const cudaError_t ec = cudaGetDeviceCount(&ndev);
+  if (ec != cudaSuccess) {
     cudaGetLastError();
-    return RERANK_ECUDA;
+    return cuda_fail(ec, "cudaGetDeviceCount");
   }
+  if (cfg->device < 0 || cfg->device >= ndev) return cuda_fail(cudaErrorInvalidDevice, "rerank_create: device index");
   cudaDeviceProp prop;
   RR_CUDA(cudaGetDeviceProperties(&prop, cfg->device));
-  if (prop.major != 10 || prop.minor != 3) return RERANK_ECUDA;
+  if (prop.major != 10 || prop.minor != 3)
+    return cuda_fail(cudaErrorNoKernelImageForDevice, "rerank_create: not a compute capability 10.3 device");
   RR_CUDA(cudaSetDevice(cfg->device));
   rerank_ctx* ctx = new (std::nothrow) rerank_ctx();
   if (!ctx) return RERANK_ENOMEM;

@@ -63,6 +63,9 @@ def test_create_without_gpu_reports_status(lib):
     with pytest.raises(rerank.RerankError) as e:
         rerank.Reranker(device=0)
     assert e.value.status == 4  # ECUDA, not a crash
+    # the failing CUDA call is named, in the status text and in the exception
+    assert "cudaGetDeviceCount" in lib.rerank_last_cuda_error().decode()
+    assert "cudaGetDeviceCount" in str(e.value)
 
 
 def _bucket(n):
