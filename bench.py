@@ -206,6 +206,39 @@ def _config(args, w):
 SIM_TRAFFIC_BYTES = {("bf16", "market"): 389.4e6}
 
 
+def _stage_rooflines(precision, stages, nq, ng, d, k1, k2, rescore_m, h_nnz, layers):
+    """Bytes each memory-side stage must move at least, against the measured
+    copy bandwidth.  normalize: the FP32 rows read once, the unit rows and
+    their low-precision copies written once (rows padded to the tile);
+    refine: the candidate rows gathered by the first rescoring batch (at
+    least 32 per row, served mostly from L2, so the fraction may pass 1);
+    propagate: per layer, the k2 + 1 message rows of every row gathered (on
+    average k2 + 1 times each input row) and the output written, CSR entries
+    of 8 bytes; rank: the ranked lists written (index + distance)."""
+    peaks, which = _peaks()
+    hbm = peaks["hbm_gbs"]
+    n = nq + ng
+    tc = precision != "fp32"
+    np_ = -(-n // (256 if tc else 128)) * (256 if tc else 128)
+    dp = -(-d // (128 if precision == "fp8" else 64)) * (128 if precision == "fp8" else 64)
+    per_el = {"fp32": 4, "bf16": 8, "fp8": 9}[precision]
+    first = min(k1 + max(rescore_m, 0), (k1 + 7) & ~3)
+    out = {}
+    byts = {"normalize": n * d * 4 + np_ * dp * per_el,
+            "refine": n * first * dp * 4,
+            "propagate": sum(((k2 + 1) * h_nnz[l - 1] + h_nnz[l]) * 8 for l in range(1, min(layers, 8) + 1)),
+            "rank": nq * ng * 8}
+    for k, b in byts.items():
+        ms = stages.get(k)
+        if not ms or b <= 0:
+            continue
+        gbs = b / (ms * 1e-3) / 1e9
+        out[k] = {"bytes": int(b), "ms": ms, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm}
+    out["peak_gbs"] = hbm
+    out["peak_source"] = f"{which} copy bandwidth"
+    return out
+
+
 def _roofline(precision, sim_ms, n, d, workload):
     """Roofline of the dominant kernel, the similarity GEMM with its fused top-K:
     2 n^2 d flops per launch (the full square; the kernel computes every tile)."""
@@ -502,6 +535,10 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "stages_ms": stages, "gpu_launches": int(launches * args.steps),
             "clocks": clocks.summary(), "autotune": tuned}
     info = R.last_info()
+    m_used = (tuned or {}).get("rescore_m", -1)
+    line["stage_rooflines"] = _stage_rooflines(args.precision, stages, nq, ng, d, k1, k2,
+                                               m_used if m_used is not None and m_used >= 0 else 16,
+                                               info["h_nnz"], L)
     line["fp64_rescored"] = info["fp64_rescored"]
     line["fallback_rows"] = info["fallback_rows"]
     line["exact_scan_rows"] = info["exact_scan_rows"]

@@ -316,7 +316,7 @@ typedef struct {
   int64_t fp64_rescored;       /* candidate scores recomputed in FP64 near a tie */
   int64_t fallback_rows;       /* rows whose first candidate list could not be certified */
   int64_t exact_scan_rows;     /* rows finally redone by the exact FP32 scan of all columns */
-  int64_t h_nnz[9];            /* nnz of h^(0) .. h^(min(L,8)) */
+  int64_t h_nnz[9];            /* nnz of h^(0) .. h^(min(L,8)); zero after a batched call */
   int64_t workspace_bytes;     /* device workspace held by the context */
   int64_t kernel_launches;     /* kernels of this library launched by the call (last attempt) */
   int32_t error_bits;          /* device error word of the last call (0 = clean) */

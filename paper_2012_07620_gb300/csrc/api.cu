@@ -369,7 +369,8 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     int src = 2;
     for (int l = 0; l < sh.layers; ++l) {
       const int dst = l & 1;
-      nl += launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, ctx->sm_count, sh.tune, s);
+      nl += launch_propagate(sh, b, src, dst, ctx->cfg.aggregator, status, ctx->sm_count, sh.tune, s, nullptr,
+                             l < 8 ? status + kStNnz0 + l + 1 : nullptr);
       src = dst;
     }
     RR_CUDA(cudaGetLastError());
@@ -420,6 +421,7 @@ rerank_status map_status(const long long* h, int precision, rerank_info* info, i
   info->exact_scan_rows = precision == RERANK_PREC_FP32 ? h[kStFallback] : h[kStFallback2];
   info->error_bits = int32_t(h[kStErr]);
   info->bad_row = h[kStBadRow] == LLONG_MAX ? -1 : int32_t(h[kStBadRow]);
+  for (int l = 0; l < 9; ++l) info->h_nnz[l] = h[kStNnz0 + l];
   const int e = int(h[kStErr]);
   *need = 0;
   if (e & (kErrNonFinite | kErrZeroNorm)) return RERANK_EINVAL;

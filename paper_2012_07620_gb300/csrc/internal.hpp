@@ -316,7 +316,7 @@ int launch_layer_compact(int64_t n, const int64_t* start, const int32_t* len, co
                          const int64_t* cstart, int32_t* ccol, float* cval, cudaStream_t s);
 int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int aggregator,
                       long long* status, int sm_count, const Tuning& t, cudaStream_t s,
-                      const LayerReuse* reuse = nullptr);
+                      const LayerReuse* reuse = nullptr, long long* nnz_slot = nullptr);
 // rows_sel (nullable): only rows with rows_sel[i] != 0 get their norm.
 int launch_row_norms(const Shape& sh, const Buffers& b, int src, const long long* status, cudaStream_t s,
                      const uint8_t* rows_sel = nullptr);

@@ -85,7 +85,7 @@ __global__ void k3_sort_count(const int32_t* __restrict__ knn, int64_t n, int k1
 __global__ void k3_fill(const int32_t* __restrict__ out_sorted, const int32_t* __restrict__ in_sorted,
                         const int32_t* __restrict__ inptr, const int32_t* __restrict__ h0ptr, int64_t n, int k1,
                         int feature, int32_t* __restrict__ col, float* __restrict__ val,
-                        int64_t* __restrict__ start, int32_t* __restrict__ len) {
+                        int64_t* __restrict__ start, int32_t* __restrict__ len, long long* __restrict__ nnz0) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int32_t* o = out_sorted + i * k1;
@@ -122,7 +122,10 @@ __global__ void k3_fill(const int32_t* __restrict__ out_sorted, const int32_t* _
   }
   start[i] = h0ptr[i];
   len[i] = pos - h0ptr[i];
-  if (i == n - 1) start[n] = pos;
+  if (i == n - 1) {
+    start[n] = pos;
+    if (nnz0) *nnz0 = pos;  // nnz of h^(0)
+  }
 }
 
 __global__ void k3_edges(const int32_t* __restrict__ knn, const float* __restrict__ score, int64_t n, int k1, int k2,
@@ -161,7 +164,6 @@ __global__ void k3_edges(const int32_t* __restrict__ knn, const float* __restric
 
 int launch_graph(const Shape& sh, const Buffers& b, float alpha, int aggregator, int feature, long long* status,
                   cudaStream_t s) {
-  (void)status;
   const int64_t n = sh.n, edges = n * sh.k1;
   const int T = 256;
   cudaMemsetAsync(b.indeg, 0, sizeof(int32_t) * n, s);
@@ -173,7 +175,8 @@ int launch_graph(const Shape& sh, const Buffers& b, float alpha, int aggregator,
                                                                b.in_sorted, b.rowcnt, feature);
   launch_scan32(b.rowcnt, n, b.h0ptr, s);
   k3_fill<<<unsigned((n + T - 1) / T), T, 0, s>>>(b.out_sorted, b.in_sorted, b.inptr, b.h0ptr, n, sh.k1, feature,
-                                                  b.col[2], b.val[2], b.start[2], b.len[2]);
+                                                  b.col[2], b.val[2], b.start[2], b.len[2],
+                                                  status ? status + kStNnz0 : nullptr);
   k3_edges<<<unsigned((n + T - 1) / T), T, 0, s>>>(b.knn_idx, b.knn_score, n, sh.k1, sh.k2, alpha, aggregator, b.nbr,
                                                    b.nbr_w, b.nbr_n);
   return 7;

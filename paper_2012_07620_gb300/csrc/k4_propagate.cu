@@ -151,7 +151,8 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
              const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ ub,
              const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen, int32_t* __restrict__ dcol,
              float* __restrict__ dval, int64_t n, int64_t cap, int32_t* __restrict__ big_rows,
-             int32_t* __restrict__ big_count, long long* __restrict__ status, bool agg_max, LayerReuse reuse) {
+             int32_t* __restrict__ big_count, long long* __restrict__ status, bool agg_max, LayerReuse reuse,
+             unsigned long long* __restrict__ nnz_out) {
   extern __shared__ int smem_i[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   volatile int* keys = smem_i + wib * WSLOTS * 2;
@@ -163,6 +164,7 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
   }
   __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
+  unsigned long long nnz = 0;  // entries this warp wrote (lane 0)
   for (int64_t i = int64_t(blockIdx.x) * nw + wib; i < n; i += int64_t(gridDim.x) * nw) {
     if (reuse.changed && !reuse.changed[i]) {
       // inputs unchanged: the known row, in its own column order
@@ -172,7 +174,10 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
         dcol[o + p] = int32_t(reuse.rcol[a + p] + reuse.shift);
         dval[o + p] = reuse.rval[a + p];
       }
-      if (lane == 0) dlen[i] = m;
+      if (lane == 0) {
+        dlen[i] = m;
+        nnz += unsigned(m);
+      }
       continue;
     }
     const int u = ub[i];
@@ -301,7 +306,10 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
       dcol[o + p] = keys[p];
       dval[o + p] = vals[p] * inv;
     }
-    if (lane == 0) dlen[i] = cnt;
+    if (lane == 0) {
+      dlen[i] = cnt;
+      nnz += unsigned(cnt);
+    }
     __syncwarp();
     for (int s = lane; s < T; s += kWarp) {
       keys[s] = KEY_EMPTY;
@@ -309,6 +317,7 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
     }
     __syncwarp();
   }
+  if (nnz_out && lane == 0 && nnz) atomicAdd(nnz_out, nnz);
 }
 
 __global__ void __launch_bounds__(BIG_THREADS)
@@ -317,7 +326,8 @@ k4_spmm_big(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen
             const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ big_rows,
             const int32_t* __restrict__ big_count, const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen,
             int32_t* __restrict__ dcol, float* __restrict__ dval, int64_t n, int64_t cap, float* __restrict__ dense,
-            uint32_t* __restrict__ bits, long long* __restrict__ status, bool agg_max) {
+            uint32_t* __restrict__ bits, long long* __restrict__ status, bool agg_max,
+            unsigned long long* __restrict__ nnz_out) {
   __shared__ int scan_s[BIG_THREADS];
   __shared__ float red_s[BIG_THREADS];
   if (!capacity_ok(dstart, n, cap, status)) return;
@@ -381,7 +391,10 @@ k4_spmm_big(const int64_t* __restrict__ sstart, const int32_t* __restrict__ slen
     }
     const float inv = 1.0f / sqrtf(red_s[0]);
     for (int p = tid; p < total; p += BIG_THREADS) dval[o + p] *= inv;
-    if (tid == 0) dlen[i] = total;
+    if (tid == 0) {
+      dlen[i] = total;
+      if (nnz_out) atomicAdd(nnz_out, (unsigned long long)total);
+    }
     __syncthreads();
   }
 }
@@ -425,7 +438,8 @@ int launch_layer_compact(int64_t n, const int64_t* start, const int32_t* len, co
 int propagate_warp_slots() { return WSLOTS; }
 
 int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int aggregator, long long* status,
-                      int sm_count, const Tuning& t, cudaStream_t s, const LayerReuse* reuse) {
+                      int sm_count, const Tuning& t, cudaStream_t s, const LayerReuse* reuse, long long* nnz_slot) {
+  unsigned long long* nnz_out = reinterpret_cast<unsigned long long*>(nnz_slot);
   const int64_t n = sh.n;
   const int k2p1 = sh.k2 + 1;
   const int T = 256;
@@ -443,12 +457,12 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
   k4_spmm_warp<<<blocks, warps * kWarp, smem, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                    b.nbr_n, k2p1, b.ub, b.start[dst], b.len[dst], b.col[dst],
                                                    b.val[dst], n, sh.cap_h, b.big_rows, b.big_count, status,
-                                                   aggregator == RERANK_AGG_MAX, ru);
+                                                   aggregator == RERANK_AGG_MAX, ru, nnz_out);
   k4_spmm_big<<<sm_count, BIG_THREADS, 0, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                b.nbr_n, k2p1, b.big_rows, b.big_count, b.start[dst], b.len[dst],
                                                b.col[dst], b.val[dst], n, sh.cap_h, b.hash_keys_vals,
                                                reinterpret_cast<uint32_t*>(b.hash_keys_vals + size_t(sm_count) * n),
-                                               status, aggregator == RERANK_AGG_MAX);
+                                               status, aggregator == RERANK_AGG_MAX, nnz_out);
   return 4;
 }
 

@@ -82,6 +82,18 @@ def test_tiny_workload(R):
     assert stats["max_dist_err"] < 1e-5
 
 
+def test_layer_nnz_reported(R):
+    """rerank_info.h_nnz: the non-zeros of h^(0) (= A*, Eq. 9-11) and of every
+    propagated layer (Eq. 14) equal the oracle's supports exactly."""
+    spec = synthetic.WorkloadSpec("nnz", 90, 800, 64, 40, 0.35, 20, None, seed=23)
+    w = synthetic.make_workload(spec)
+    ref = o.rerank(w.xq, w.xg, k1=20, k2=6, layers=3, mode="sparse")
+    _gpu(R, w.xq, w.xg, 20, 6, 3)
+    got = R.last_info()["h_nnz"]
+    want = [ref.a_star.nnz] + [h.nnz for h in ref.h[1:]]
+    assert got[:4] == want and got[4:] == [0] * 5, (got, want)
+
+
 @pytest.mark.parametrize("nq,ng,d,c,k1,k2,layers", [
     (37, 300, 64, 20, 10, 3, 1),
     (129, 1200, 200, 60, 26, 7, 2),
