@@ -323,7 +323,10 @@ __global__ void __launch_bounds__(256) k0_normalize_vec(const float* __restrict_
 int launch_normalize(const Shape& sh, const void* xq, const void* xg, float* xhat, double* norm, void* xlow,
                      __nv_bfloat16* xhi, __nv_bfloat16* xlo, float* inv_scale, float* err, float* emax,
                      int precision, long long* status, cudaStream_t s) {
-  const int threads = 256;
+  // The register-resident row (about 96 registers a thread) allows 5 CTAs of
+  // 128 threads per SM (20 warps) against 2 of 256 (16 warps).
+  const bool vec_shape = sh.dtype == RERANK_DTYPE_F32 && sh.d % 4 == 0 && sh.dp <= 4 * kWarp * NV4;
+  const int threads = vec_shape ? 128 : 256;
   const unsigned blocks = unsigned((sh.np * kWarp + threads - 1) / threads);
   const bool vec = sh.dtype == RERANK_DTYPE_F32 && sh.d % 4 == 0 && sh.dp <= 4 * kWarp * NV4 &&
                    (reinterpret_cast<uintptr_t>(xq) & 15) == 0 && (reinterpret_cast<uintptr_t>(xg) & 15) == 0;
