@@ -1,7 +1,8 @@
 """The ctypes mirrors in rerank.py have the layout of the C structs in
-include/rerank.h: same size, every field at the same offset.  A mismatch
-would pass garbage across the boundary without any error, so the check
-compiles the header with the host C compiler and compares (no GPU)."""
+include/rerank.h (same size, every field at the same offset) and the same
+status and enum values.  A mismatch would pass garbage across the boundary
+without any error, so the checks compile the header with the host C compiler
+and compare (no GPU)."""
 import ctypes
 import shutil
 import subprocess
@@ -50,3 +51,26 @@ def test_ctypes_mirrors_match_the_header(tmp_path):
         assert c[(cname, ".")] == ctypes.sizeof(py), cname
         for field, _ in py._fields_:
             assert c[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_python_constants_match_the_header(tmp_path):
+    """Status codes and the enum values the binding passes by number."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    names = {f"RERANK_{v}": k for k, v in rerank.STATUS_NAMES.items()}
+    names.update({f"RERANK_PREC_{k.upper()}": v for k, v in rerank.PRECISION.items()})
+    names.update({f"RERANK_DTYPE_{k.upper()}": v for k, v in rerank.DTYPE.items()})
+    names.update({f"RERANK_AGG_{k.upper()}": v for k, v in rerank.AGGREGATOR.items()})
+    names.update({f"RERANK_FEAT_{k.upper()}": v for k, v in rerank.FEATURE.items()})
+    names.update({f"RERANK_DBG_{k.upper()}": v for k, v in rerank.DEBUG.items()})
+    lines = ["#include <stdio.h>", '#include "rerank.h"', "int main(void) {"]
+    lines += [f'  printf("{n} %d\\n", (int){n});' for n in names]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", f"-I{build.INCLUDE}", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {n: int(v) for n, v in (line.split() for line in out.splitlines())}
+    assert got == names
