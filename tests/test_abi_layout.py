@@ -74,3 +74,16 @@ def test_python_constants_match_the_header(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
     got = {n: int(v) for n, v in (line.split() for line in out.splitlines())}
     assert got == names
+
+
+def test_header_compiles_as_c_and_cpp(tmp_path):
+    """The boundary is plain C with extern "C" guards: both compilers accept it
+    with warnings as errors."""
+    for cc, std, ext in (("gcc", "-std=c99", "c"), ("g++", "-std=c++17", "cpp")):
+        exe = shutil.which(cc)
+        if exe is None:
+            pytest.skip(f"no {cc}")
+        src = tmp_path / f"h.{ext}"
+        src.write_text('#include "rerank.h"\nint main(void) { return RERANK_OK; }\n')
+        subprocess.run([exe, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", f"-I{build.INCLUDE}", str(src)],
+                       check=True)
