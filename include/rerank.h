@@ -276,7 +276,9 @@ rerank_status rerank_tuning_lookup(const char* path, int precision, int64_t n, i
  *   x          n x d features (dtype)
  *   out_idx    n x k int32, sorted by (S desc, index asc); out_idx[i*k] == i
  *              unless a lower-indexed vertex has exactly the same direction
- *   out_score  n x k float: S of each listed pair (FP32-accurate, see DESIGN)
+ *   out_score  n x k float: S of each listed pair, the FP32 dot product of the
+ *              unit rows: |out_score - S| <= (d_p/32 + 10) * 2^-24 * 1.01 with
+ *              d_p = d rounded up to 64 (pairs near a tie are recomputed in FP64)
  * Errors: as rerank_run. */
 rerank_status rerank_knn(rerank_ctx* ctx, const void* x, int64_t n, int d, int dtype, int k,
                          int32_t* out_idx, float* out_score, void* stream);
@@ -292,16 +294,22 @@ rerank_status rerank_knn(rerank_ctx* ctx, const void* x, int64_t n, int d, int d
  * library keeps until the process exits.
  *
  *   x, out_idx, out_score, n, d, dtype, k: as rerank_knn, but all three buffers
- *   must be device memory (EINVAL otherwise).
+ *   must be device memory of the current device, or managed memory (EINVAL
+ *   otherwise: host memory, or memory of another GPU).
  * Limits: n <= RERANK_KNN_NOALLOC_MAX_N, d <= RERANK_KNN_NOALLOC_MAX_D,
  * k <= RERANK_KNN_NOALLOC_MAX_K; larger sizes return EBUDGET and nothing runs.
  * The first call on a device looks up the scratch area's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is kept for the life of the process: do not call this entry
+ * point again on a device after cudaDeviceReset of that device.
  * All calls share the one scratch area: two calls whose work overlaps on the
  * GPU (for instance on two streams, or from two host threads) race and give
  * wrong results.  Calls on one stream, one after another, are safe.  The call
  * returns after a stream synchronisation, with the status of the device work.
- * Errors: EINVAL, EBUDGET, ECUDA, EINTERNAL as for rerank_knn. */
+ * Errors: EINVAL (arguments, host or foreign-device buffers, non-finite or
+ * zero rows), EBUDGET (sizes over the limits), ECUDA (a CUDA call failed),
+ * ETIMEOUT (a bounded device wait ran out), EUNSUPPORTED (device index 64 or
+ * higher), EINTERNAL (a result could not be certified). */
 #define RERANK_KNN_NOALLOC_SCRATCH_BYTES (13u << 20)
 #define RERANK_KNN_NOALLOC_MAX_N 4096
 #define RERANK_KNN_NOALLOC_MAX_D 256

@@ -22,8 +22,7 @@ Library primitives (matrix products, sparse products, stable sorts) serve as
 single steps; nothing is blocked, fused or reordered beyond chunking the rows
 of S so that an N x N matrix need not be held at once.
 
-Readings of points the paper leaves open (each one is also listed in the
-design notes):
+Readings of points the paper leaves open:
   * self is a candidate of its own neighbourhood and S_ii := 1 exactly, so
     vertex i is first in N(i, k);
   * ties in every ordering (neighbour lists, final ranking) go to the lower

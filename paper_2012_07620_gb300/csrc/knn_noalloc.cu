@@ -69,13 +69,16 @@ rerank_status scratch_address(int dev, unsigned char** out) {
   return RERANK_OK;
 }
 
-bool on_device(const void* p) {
+// Device memory of device `dev` (or managed memory): a buffer on another GPU
+// would be a peer access from these kernels, which faults without peer access.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -89,12 +92,10 @@ extern "C" rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int
   if (n < 1 || d < 1 || k < 1 || k > n || (dtype != RERANK_DTYPE_F32 && dtype != RERANK_DTYPE_BF16))
     return RERANK_EINVAL;
   if (n > kMaxN || d > kMaxD || k > kMaxK) return RERANK_EBUDGET;
-  if (!on_device(x) || !on_device(out_idx) || !on_device(out_score)) return RERANK_EINVAL;
-  if (fallback_warps() != kFbWarps) return RERANK_EINTERNAL;
   int dev = 0;
   RR_CUDA(cudaGetDevice(&dev));
-  int sms = 0;
-  RR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!on_device(x, dev) || !on_device(out_idx, dev) || !on_device(out_score, dev)) return RERANK_EINVAL;
+  if (fallback_warps() != kFbWarps) return RERANK_EINTERNAL;
   unsigned char* base = nullptr;
   rerank_status st = scratch_address(dev, &base);
   if (st != RERANK_OK) return st;
@@ -123,7 +124,6 @@ extern "C" rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int
   int32_t* fb_rows = reinterpret_cast<int32_t*>(base + kOffFbRows);
   float* fb_s = reinterpret_cast<float*>(base + kOffFbS);
   int32_t* fb_i = reinterpret_cast<int32_t*>(base + kOffFbI);
-  (void)sms;
 
   noalloc_reset<<<1, 64, 0, s>>>(status, fb_count);
   launch_normalize(sh, x, x, xhat, norm, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, RERANK_PREC_FP32,

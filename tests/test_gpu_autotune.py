@@ -74,3 +74,29 @@ def test_every_launch_shape_gives_the_same_result(lib, data, tmp_path, precision
         a = _run(D, xq, xg)
         b = _run(R, xq, xg)
     assert (a[0] == b[0]).all() and (a[1] == b[1]).all()
+
+
+@pytest.fixture(scope="module")
+def oracle_ref():
+    from oracle import rerank_oracle as o
+    w = synthetic.make_workload(SPEC)
+    return o.rerank(w.xq, w.xg, k1=26, k2=7, layers=2, mode="sparse")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "fp8"])
+def test_tuned_path_matches_oracle(lib, data, tmp_path, oracle_ref, precision):
+    """The launch shapes the autotuner picks give Algorithm 1's result: the
+    tuned run's neighbour lists (Eq. 8) and ranked lists (Alg. 1 step 7)
+    against the FP64 oracle on the same instance."""
+    import parity
+    xq, xg = data
+    path = str(tmp_path / "tune.json")
+    with lib.Reranker(precision=precision, autotune_path=path) as R:
+        R.autotune(xq, xg, 26, 7, 2)
+        idx, dist = _run(R, xq, xg)
+        knn = R.debug("knn_idx").reshape(SPEC.n, 26)
+    w = synthetic.make_workload(SPEC)
+    from oracle import rerank_oracle as o
+    xu_hat = o.unit_rows(np.concatenate([w.xq, w.xg]))
+    parity.assert_knn_equal(knn, oracle_ref.knn_idx, oracle_ref.knn_score, xu_hat)
+    parity.assert_ranked_equal(idx, dist, oracle_ref.s, oracle_ref.idx)
