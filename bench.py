@@ -11,16 +11,18 @@ ranked lists (every gallery index per query).
 Prints one JSON line.  `value` is ms per re-rank with inputs resident in HBM
 on the BF16 tensor-core path (FP32 rescoring, exact neighbour lists), timed
 with CUDA events on the launching stream, L2 flushed before every step;
-`fp32_path` is the plain FP32 path on the same instance; `e2e` is the same
-re-rank through the C ABI with pinned host buffers (copies inside the timed
-region); `serving` is a short Poisson session (200 req/s) against the
-resident 40k-vector gallery with its p50/p99 latency.  `--workload
-batched64` times 64 independent instances per rerank_run_batch call against
-64 sequential calls; `--workload serving` runs the full 60 s session.
+`e2e` is the same re-rank through the C ABI with pinned host buffers (copies
+inside the timed region).  At N = 1 the line also carries, each with its own
+roofline: `fp32_path` and `fp8_path` (the other precisions on the same
+instance), `large_50k` (5,000 + 45,000 vectors, d = 512, in BF16, FP8 and
+FP32), `batched64` (64 independent instances per rerank_run_batch call
+against 64 sequential calls), `serving` (a 60 s Poisson session at 200 req/s
+against the resident 40k-vector gallery, p50/p99 latency) and `cpu_baseline`
+(the FP64 oracle's whole Algorithm 1 on the same instance on the host cores).
 With N > 1 (torchrun) every rank runs an independent replica (the method
 needs no exchange between instances), the time is the max over ranks and
 `value` divides it by all ranks' re-ranks.  `--impl reference` times the
-FP64 oracle on the host cores instead.
+FP64 oracle's whole Algorithm 1 on the host cores instead.
 """
 from __future__ import annotations
 
@@ -141,51 +143,87 @@ def _max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def cpu_oracle_sample(xq, xg, k1, target_s=15.0):
-    """Time the FP64 oracle's Eq. 7-8 (S rows + full sort + top-k1) on a bounded
-    sample of rows, scaled to all N rows.  Returns (ms per re-rank, sample text, threads)."""
-    from oracle import rerank_oracle
-    xu = np.concatenate([xq, xg]).astype(np.float64)
-    n = xu.shape[0]
-    rows = 64
-    t0 = time.perf_counter()
-    rerank_oracle.knn_lists(xu, k1, rows=np.arange(rows))
-    dt = time.perf_counter() - t0
-    rows = int(min(n, max(64, rows * target_s / max(dt, 1e-3) * 0.8)))
-    t0 = time.perf_counter()
-    rerank_oracle.knn_lists(xu, k1, rows=np.arange(rows))
-    dt = time.perf_counter() - t0
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _blas_threads():
     threads = os.cpu_count()
     try:
         from threadpoolctl import threadpool_info
         threads = max((i.get("num_threads", 1) for i in threadpool_info()), default=threads)
     except ImportError:
         pass
-    sample = (f"oracle Eq. 7-8 (FP64 S rows, stable full sort, top-k1) on {rows} of {n} rows, "
-              f"{dt:.1f} s, scaled x{n / rows:.2f}; graph, propagation and ranking not included")
-    return dt * 1e3 * n / rows, sample, threads
+    return threads
+
+
+def cpu_oracle_full(xq, xg, k1, k2, layers):
+    """One run of the FP64 oracle's whole Algorithm 1 (sparse mode: Eq. 7-8 S
+    rows with a full stable sort per row, A and A*, k2-edge weights, L layers
+    of Eq. 14, cos(h_q, h_g) and a full stable sort per query) on the real
+    instance, on the host cores.  Returns (ms, per-stage ms)."""
+    from oracle import rerank_oracle
+    t = {}
+    t0 = time.perf_counter()
+    rerank_oracle.rerank(xq, xg, k1=k1, k2=k2, layers=layers, mode="sparse", timings=t)
+    ms = (time.perf_counter() - t0) * 1e3
+    return ms, {k: v * 1e3 for k, v in t.items()}
+
+
+def _cpu_sample_text(n, nq, ng, d):
+    return (f"whole Algorithm 1 by the FP64 oracle (sparse mode) on the full instance, {nq} + {ng} = {n} "
+            f"vectors, d={d}: no row sampling, no scaling; {os.cpu_count()} host cores "
+            f"({_cpu_model()}); BLAS threads {_blas_threads()}, per-row sorts single-threaded")
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the oracle's whole Algorithm 1, one run per step.  A
+    run takes tens of seconds, so the arm runs as many of the requested
+    warm-up steps as fit in a quarter of --ref-seconds (at least one) and as
+    many timed steps as fit in the rest (at least one), and reports the counts
+    it really ran."""
     from paper_2012_07620_gb300 import synthetic
     wl = WORKLOADS[args.workload]
     if rank != 0:
         return
     w = synthetic.make_workload(getattr(synthetic, wl["spec"]))
-    vals = []
-    sample = ""
-    threads = os.cpu_count()
+    k1, k2, L = wl["k1"], wl["k2"], wl["layers"]
+    t_start = time.perf_counter()
+    warm, run_ms = 0, None
     for _ in range(args.warmup):
-        pass
+        # warm-ups take at most a quarter of the budget (the first one always runs)
+        if run_ms is not None and (time.perf_counter() - t_start) + run_ms / 1e3 > args.ref_seconds / 4:
+            break
+        run_ms, _ = cpu_oracle_full(w.xq, w.xg, k1, k2, L)
+        warm += 1
+    vals, stages = [], {}
     for _ in range(args.steps):
-        v, sample, threads = cpu_oracle_sample(w.xq, w.xg, wl["k1"], target_s=args.cpu_seconds)
+        if vals and (time.perf_counter() - t_start) + float(np.mean(vals)) / 1e3 > args.ref_seconds:
+            break
+        v, st = cpu_oracle_full(w.xq, w.xg, k1, k2, L)
         vals.append(v)
+        for k, x in st.items():
+            stages[k] = stages.get(k, 0.0) + x
     ms = float(np.mean(vals))
+    stages = {k: x / len(vals) for k, x in stages.items()}
+    n, d = len(w.xq) + len(w.xg), w.spec.dim
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "steps": len(vals), "warmup": warm, "ms_per_step": ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(args, w), "cpu_baseline": {"value": ms, "unit": "ms", "cores": threads,
-                                                          "kind": "oracle", "sample": sample},
+            "config": _config(args, w),
+            "requested": {"steps": args.steps, "warmup": args.warmup, "budget_s": args.ref_seconds},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": _blas_threads(), "kind": "oracle",
+                             "sample": _cpu_sample_text(n, len(w.xq), len(w.xg), d), "stages_ms": stages,
+                             "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -204,17 +242,21 @@ def _config(args, w):
 # (profiles/k1_tc_topk_bf16_market_23k_d2048.md); None where no capture of the
 # current kernel exists.
 SIM_TRAFFIC_BYTES = {("bf16", "market"): 389.4e6}
+# DRAM bytes of the refinement's first pass, same source
+# (profiles/k2_refine_bf16_market_23k_d2048.md).
+REFINE_DRAM_BYTES = {("bf16", "market"): 1.599e9}
 
 
-def _stage_rooflines(precision, stages, nq, ng, d, k1, k2, rescore_m, h_nnz, layers):
+def _stage_rooflines(precision, stages, nq, ng, d, k1, k2, rescore_m, h_nnz, layers, workload):
     """Bytes each memory-side stage must move at least, against the measured
     copy bandwidth.  normalize: the FP32 rows read once, the unit rows and
     their low-precision copies written once (rows padded to the tile);
-    refine: the candidate rows gathered by the first rescoring batch (at
-    least 32 per row, served mostly from L2, so the fraction may pass 1);
     propagate: per layer, the k2 + 1 message rows of every row gathered (on
     average k2 + 1 times each input row) and the output written, CSR entries
-    of 8 bytes; rank: the ranked lists written (index + distance)."""
+    of 8 bytes; rank: the ranked lists written (index + distance).
+    refine is a gather: its floor is every distinct FP32 unit row read once
+    (N d_p 4 bytes); the rows its first rescoring batch gathers (most served
+    by L1/L2) are reported as a gather rate, not as a fraction of HBM."""
     peaks, which = _peaks()
     hbm = peaks["hbm_gbs"]
     n = nq + ng
@@ -225,7 +267,6 @@ def _stage_rooflines(precision, stages, nq, ng, d, k1, k2, rescore_m, h_nnz, lay
     first = min(k1 + max(rescore_m, 0), (k1 + 7) & ~3)
     out = {}
     byts = {"normalize": n * d * 4 + np_ * dp * per_el,
-            "refine": n * first * dp * 4,
             "propagate": sum(((k2 + 1) * h_nnz[l - 1] + h_nnz[l]) * 8 for l in range(1, min(layers, 8) + 1)),
             "rank": nq * ng * 8}
     for k, b in byts.items():
@@ -234,6 +275,15 @@ def _stage_rooflines(precision, stages, nq, ng, d, k1, k2, rescore_m, h_nnz, lay
             continue
         gbs = b / (ms * 1e-3) / 1e9
         out[k] = {"bytes": int(b), "ms": ms, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm}
+    ms = stages.get("refine")
+    if ms:
+        floor = n * dp * 4
+        gathered = n * first * dp * 4
+        out["refine"] = {"ms": ms, "floor_bytes": int(floor),
+                         "floor_frac_of_hbm": floor / (ms * 1e-3) / 1e9 / hbm,
+                         "gathered_bytes": int(gathered), "gather_rate_gbs": gathered / (ms * 1e-3) / 1e9,
+                         "dram_bytes_ncu": REFINE_DRAM_BYTES.get((precision, workload)),
+                         "note": "gather rate of candidate rows (mostly L1/L2 hits), not an HBM fraction"}
     out["peak_gbs"] = hbm
     out["peak_source"] = f"{which} copy bandwidth"
     return out
@@ -261,16 +311,78 @@ def _roofline(precision, sim_ms, n, d, workload):
     return roof
 
 
-def run_batched(args, world, rank, local):
+def _tune(rerank, local, precision, xq, xg, k1, k2, L, path):
+    """Launch shapes from the autotuner, measured on this instance before any timed region."""
+    T = rerank.Reranker(device=local, precision=precision, autotune_path=path)
+    tuned = T.autotune(xq, xg, k1, k2, L)
+    T.close()
+    return tuned
+
+
+def _time_instance(rerank, local, precision, xq, xg, k1, k2, L, steps, warmup, stream, flush, tune_path,
+                   world=1):
+    """CUDA-event time of `steps` re-ranks (after `warmup`), L2 flushed before
+    each; per-stage times from the library's own events.  Returns a dict."""
+    import torch
+    nq, ng = xq.shape[0], xg.shape[0]
+    out_i = torch.empty((nq, ng), dtype=torch.int32, device=xq.device)
+    out_d = torch.empty((nq, ng), dtype=torch.float32, device=xq.device)
+    R = rerank.Reranker(device=local, precision=precision, stage_timing=True, autotune_path=tune_path)
+    for _ in range(warmup):
+        R.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
+    launches = R.last_info()["kernel_launches"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stage_sum = {}
+    _barrier(world)
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.fill_(s & 255)
+        ev[s][0].record(stream)
+        R.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
+        ev[s][1].record(stream)
+        for k, v in R.stage_times().items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    _barrier(world)
+    total = _max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world)
+    info = R.last_info()
+    R.close()
+    return {"ms": total / steps, "stages_ms": {k: v / steps for k, v in stage_sum.items()}, "steps": steps,
+            "launches_per_step": int(launches), "fp64_rescored": info["fp64_rescored"],
+            "fallback_rows": info["fallback_rows"], "exact_scan_rows": info["exact_scan_rows"],
+            "h_nnz": info["h_nnz"]}
+
+
+def measure_workload(rerank, synthetic, local, dev, spec_name, precisions, steps, warmup, stream, flush,
+                     tune_dir, k1=26, k2=7, L=2, workload_key="market"):
+    """Each precision on one workload (autotuned first), with its roofline."""
+    import torch
+    w = synthetic.make_workload(getattr(synthetic, spec_name))
+    xq = torch.from_numpy(w.xq).to(dev)
+    xg = torch.from_numpy(w.xg).to(dev)
+    nq, ng, d = len(w.xq), len(w.xg), w.spec.dim
+    res = {"workload": f"{w.spec.name}: {nq} queries + {ng} gallery, d={d}, {w.spec.n_clusters} clusters + "
+                       f"{w.spec.n_distractors} distractors, k1={k1}, k2={k2}, L={L}, full ranked lists"}
+    for prec in precisions:
+        path = os.path.join(tune_dir, f"tune_{spec_name}_{prec}.json")
+        with ClockSampler(local) as clocks:
+            tuned = _tune(rerank, local, prec, xq, xg, k1, k2, L, path)
+            st = steps if prec != "fp32" else max(1, min(steps, 5))
+            r = _time_instance(rerank, local, prec, xq, xg, k1, k2, L, st, warmup, stream, flush, path)
+        r["roofline"] = _roofline(prec, r["stages_ms"].get("similarity_topk", float("nan")), nq + ng, d,
+                                  workload_key)
+        r["autotune"] = tuned
+        r["clocks"] = clocks.summary()
+        res[prec] = r
+    del xq, xg
+    torch.cuda.empty_cache()
+    return res
+
+
+def batched_measure(rerank, synthetic, local, dev, precision, steps, warmup, stream, flush, world=1):
     """64 independent instances (N log-uniform 500-8000, d in {256, 512, 2048}, BF16 features)
     per step through one rerank_run_batch call; beside it the same 64 as sequential rerank_run calls."""
     import torch
-    import __graft_entry__
-    from paper_2012_07620_gb300 import rerank, synthetic
-
-    __graft_entry__.build()
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     specs = synthetic.batched_specs()
     jobs, host = [], []
     for s in specs:
@@ -285,11 +397,10 @@ def run_batched(args, world, rank, local):
                          out_idx=torch.empty((nq, ng), dtype=torch.int32).pin_memory(),
                          out_dist=torch.empty((nq, ng), dtype=torch.float32).pin_memory()))
     flops = sum(2.0 * (j["xq"].shape[0] + j["xg"].shape[0]) ** 2 * j["xq"].shape[1] for j in jobs)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     # Launch shapes from the autotuner: one tuning run per (d, half-octave of N) among the instances.
     tune_path = os.path.join(tempfile.mkdtemp(), "tune.json")
     t_tune = time.perf_counter()
-    T = rerank.Reranker(device=local, precision=args.precision, autotune_path=tune_path)
+    T = rerank.Reranker(device=local, precision=precision, autotune_path=tune_path)
     seen = set()
     for j in jobs:
         n = j["xq"].shape[0] + j["xg"].shape[0]
@@ -299,23 +410,22 @@ def run_batched(args, world, rank, local):
             T.autotune(j["xq"], j["xg"], j["k1"], j["k2"], j["layers"])
     T.close()
     t_tune = time.perf_counter() - t_tune
-    R = rerank.Reranker(device=local, precision=args.precision, autotune_path=tune_path)
-    stream = torch.cuda.current_stream(dev)
+    R = rerank.Reranker(device=local, precision=precision, autotune_path=tune_path)
 
     def timed(fn):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for _ in range(args.warmup):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for _ in range(warmup):
             fn()
         _barrier(world)
         torch.cuda.synchronize()
-        for s in range(args.steps):
+        for s in range(steps):
             flush.fill_(s & 255)
             ev[s][0].record(stream)
             fn()
             ev[s][1].record(stream)
         torch.cuda.synchronize()
         _barrier(world)
-        return _max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world) / args.steps
+        return _max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), world) / steps
 
     def sequential():
         for j in jobs:
@@ -328,34 +438,53 @@ def run_batched(args, world, rank, local):
     R.run_batch(host, stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(1, min(steps, 5))
     for _ in range(e2e_steps):
         R.run_batch(host, stream)
     e2e_ms = _max_over_ranks((time.perf_counter() - t0) * 1e3 / e2e_steps, world)
+    R.close()
     peaks, which = _peaks()
     n_tot = sum(j["xq"].shape[0] + j["xg"].shape[0] for j in jobs)
-    line = {"metric": "ms per batch of 64 independent re-ranks (rerank_run_batch) vs 64 sequential rerank_run",
-            "value": batch_ms / world, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": batch_ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": f"64 instances, N log-uniform 500-8000 (total {n_tot}), d in {{256, 512, 2048}}, "
-                                   "BF16 features, k1 20-30, k2 5-7, 1-3 layers, full ranked lists",
-                       "gemm_tflop": flops / 1e12, "l2": "flushed before every step (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
-            "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / batch_ms,
-            "autotune": {"entries": len(seen), "seconds": t_tune},
+    return {"batch_ms": batch_ms, "sequential_ms": seq_ms, "speedup_vs_sequential": seq_ms / batch_ms,
+            "steps": steps, "launches_per_step": int(launches),
+            "workload": f"64 instances, N log-uniform 500-8000 (total {n_tot}), d in {{256, 512, 2048}}, "
+                        "BF16 features, k1 20-30, k2 5-7, 1-3 layers, full ranked lists",
+            "gemm_tflop": flops / 1e12, "autotune": {"entries": len(seen), "seconds": t_tune},
             "instances_per_s": 64.0 * world / (batch_ms * 1e-3),
             "e2e": {"value": e2e_ms, "unit": "ms",
                     "h2d_bytes_per_step": int(sum(h["xq"].numel() * 2 + h["xg"].numel() * 2 for h in host)),
                     "d2h_bytes_per_step": int(sum(h["out_idx"].numel() * 8 for h in host))},
-            "gpu_launches": int(launches * args.steps), "clocks": clocks.summary(),
+            "clocks": clocks.summary(),
             "roofline": {"bound": "tensor", "achieved": flops / (batch_ms * 1e-3) / 1e12,
                          "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": flops / (batch_ms * 1e-3) / 1e12 / peaks["bf16_tflops"], "traffic": None,
                          "kernel": "whole batch (GEMM flops / batch time)", "peak_source": f"{which} bf16 burst"}}
+
+
+def run_batched(args, world, rank, local):
+    import torch
+    import __graft_entry__
+    from paper_2012_07620_gb300 import rerank, synthetic
+
+    __graft_entry__.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    b = batched_measure(rerank, synthetic, local, dev, args.precision, args.steps, args.warmup, stream, flush,
+                        world)
+    line = {"metric": "ms per batch of 64 independent re-ranks (rerank_run_batch) vs 64 sequential rerank_run",
+            "value": b["batch_ms"] / world, "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["batch_ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": b["workload"], "gemm_tflop": b["gemm_tflop"],
+                       "l2": "flushed before every step (256 MiB write)", "parallelism": f"replicas x{world}"},
+            "sequential_ms": b["sequential_ms"], "speedup_vs_sequential": b["speedup_vs_sequential"],
+            "autotune": b["autotune"], "instances_per_s": b["instances_per_s"], "e2e": b["e2e"],
+            "gpu_launches": int(b["launches_per_step"] * args.steps), "clocks": b["clocks"],
+            "roofline": b["roofline"]}
     if rank == 0:
         print(json.dumps(line))
-    R.close()
 
 
 def serving_session(rerank, synthetic, dev, seconds, rate=200.0, precision="bf16", slots=0, stream=None):
@@ -470,17 +599,15 @@ def run_ours(args, world, rank, local):
     out_d = torch.empty((nq, ng), dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    tune_dir = tempfile.mkdtemp()
     tune_path, tuned = None, None
     if args.tune_file and os.path.exists(args.tune_file):
         # Launch shapes from an earlier run's table (e.g. to profile the shapes a bench run chose).
         tune_path = args.tune_file
         tuned = rerank.tuning_lookup(tune_path, args.precision, nq + ng, d)
     elif not args.no_autotune:
-        # Launch shapes from the autotuner, measured on this instance before the timed region.
-        tune_path = args.tune_file or os.path.join(tempfile.mkdtemp(), "tune.json")
-        T = rerank.Reranker(device=local, precision=args.precision, autotune_path=tune_path)
-        tuned = T.autotune(xq, xg, k1, k2, L)
-        T.close()
+        tune_path = args.tune_file or os.path.join(tune_dir, "tune.json")
+        tuned = _tune(rerank, local, args.precision, xq, xg, k1, k2, L, tune_path)
     R = rerank.Reranker(device=local, precision=args.precision, stage_timing=True, autotune_path=tune_path)
 
     for _ in range(args.warmup):
@@ -538,49 +665,51 @@ def run_ours(args, world, rank, local):
     m_used = (tuned or {}).get("rescore_m", -1)
     line["stage_rooflines"] = _stage_rooflines(args.precision, stages, nq, ng, d, k1, k2,
                                                m_used if m_used is not None and m_used >= 0 else 16,
-                                               info["h_nnz"], L)
+                                               info["h_nnz"], L, args.workload)
     line["fp64_rescored"] = info["fp64_rescored"]
     line["fallback_rows"] = info["fallback_rows"]
     line["exact_scan_rows"] = info["exact_scan_rows"]
     R.close()
-    if args.precision != "fp32" and not args.no_fp32_path:
-        # The plain FP32 path on the same instance, for the FP32-vs-BF16 comparison.
-        ftune = None
-        if not args.no_autotune:
-            ftune = os.path.join(os.path.dirname(tune_path), "tune_fp32.json")
-            T = rerank.Reranker(device=local, precision="fp32", autotune_path=ftune)
-            T.autotune(xq, xg, k1, k2, L)
-            T.close()
-        F = rerank.Reranker(device=local, precision="fp32", stage_timing=True, autotune_path=ftune)
-        for _ in range(args.warmup):
-            F.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
-        fsteps = max(1, min(args.steps, 5))
-        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(fsteps)]
-        fst = {}
-        torch.cuda.synchronize()
-        for k in range(fsteps):
-            flush.fill_(k & 255)
-            fev[k][0].record(stream)
-            F.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
-            fev[k][1].record(stream)
-            for a, v in F.stage_times().items():
-                fst[a] = fst.get(a, 0.0) + v / fsteps
-        torch.cuda.synchronize()
-        fms = sum(a.elapsed_time(b) for a, b in fev) / fsteps
-        line["fp32_path"] = {"ms": fms, "stages_ms": fst,
-                             "roofline": _roofline("fp32", fst.get("similarity_topk", float("nan")), n, d,
-                                                   args.workload),
-                             "bf16_speedup": fms / ms}
-        F.close()
-    if rank == 0 and args.serve_seconds_default > 0 and args.workload == "market":
+    del hq, hg, ho_i, ho_d, out_i, out_d
+    extras = world == 1 and not args.no_extras
+    if extras:
+        # The other precisions on the same instance, each autotuned, with its own roofline.
+        for prec in ("fp32", "fp8"):
+            if prec == args.precision or (prec == "fp32" and args.no_fp32_path):
+                continue
+            path = os.path.join(tune_dir, f"tune_{prec}.json")
+            with ClockSampler(local) as ck:
+                ptuned = _tune(rerank, local, prec, xq, xg, k1, k2, L, path)
+                r = _time_instance(rerank, local, prec, xq, xg, k1, k2, L,
+                                   args.steps if prec != "fp32" else max(1, min(args.steps, 5)),
+                                   args.warmup, stream, flush, path)
+            r["roofline"] = _roofline(prec, r["stages_ms"].get("similarity_topk", float("nan")), n, d,
+                                      args.workload)
+            r["autotune"] = ptuned
+            r["clocks"] = ck.summary()
+            r[f"speedup_of_{args.precision}"] = r["ms"] / ms
+            line[f"{prec}_path"] = r
+    del xq, xg
+    torch.cuda.empty_cache()
+    if extras and args.workload == "market":
+        line["large_50k"] = measure_workload(rerank, synthetic, local, dev, "LARGE_50K", ("bf16", "fp8", "fp32"),
+                                             args.steps, args.warmup, stream, flush, tune_dir,
+                                             workload_key="large50k")
+        torch.cuda.empty_cache()
+        b = batched_measure(rerank, synthetic, local, dev, "bf16", args.steps, args.warmup, stream, flush)
+        line["batched64"] = b
+        torch.cuda.empty_cache()
+    if extras and args.serve_seconds_default > 0 and args.workload == "market":
         try:
             line["serving"] = serving_session(rerank, synthetic, dev, args.serve_seconds_default,
                                               precision=args.precision if args.precision != "fp32" else "bf16")
         except Exception as e:  # reported, never fatal for the headline line
             line["serving"] = {"error": repr(e)}
-    if rank == 0 and not args.no_cpu_baseline:
-        v, sample, threads = cpu_oracle_sample(w.xq, w.xg, k1, target_s=args.cpu_seconds)
-        line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": threads, "kind": "oracle", "sample": sample}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, st = cpu_oracle_full(w.xq, w.xg, k1, k2, L)
+        line["cpu_baseline"] = {"value": v, "unit": "ms", "cores": _blas_threads(), "kind": "oracle",
+                                "sample": _cpu_sample_text(n, nq, ng, d), "stages_ms": st,
+                                "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
     if rank == 0:
         print(json.dumps(line))
 
@@ -631,10 +760,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--workload", default="market", choices=list(WORKLOADS))
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=200.0,
+                    help="reference arm: wall-time budget for its warm-up and timed oracle runs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline line: no other precisions, 50k, batched or serving keys")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
-    ap.add_argument("--serve-seconds-default", type=float, default=10.0,
+    ap.add_argument("--serve-seconds-default", type=float, default=60.0,
                     help="length of the serving session added to the market line (0 = none)")
     ap.add_argument("--no-fp32-path", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of autotuned ones")

@@ -42,6 +42,7 @@ CSR matrices.  They agree to rounding.
 from __future__ import annotations
 
 import dataclasses
+import time
 from typing import Optional
 
 import numpy as np
@@ -188,13 +189,25 @@ class OracleResult:
 
 
 def rerank(xq: np.ndarray, xg: np.ndarray, k1: int, k2: int, layers: int, alpha: float = 2.0,
-           aggregator: str = "sum", feature: str = "astar", mode: str = "auto") -> OracleResult:
+           aggregator: str = "sum", feature: str = "astar", mode: str = "auto",
+           timings: Optional[dict] = None) -> OracleResult:
     """Algorithm 1 end to end in float64.
 
     ``xq`` (Q, d) and ``xg`` (G, d) are the raw features; X_u stacks them,
     queries first.  ``mode`` is "dense", "sparse" or "auto" (dense up to 2,000
-    vertices).
+    vertices).  When ``timings`` is a dict, the wall time (s) of each group of
+    steps is stored in it: "knn" (Eq. 7-8), "graph" (Eq. 8-12), "propagate"
+    (Eq. 13-14, all layers), "rank" (Alg. 1 step 7); the arithmetic is the
+    same either way.
     """
+    clock = [time.perf_counter()]
+
+    def lap(name):
+        now = time.perf_counter()
+        if timings is not None:
+            timings[name] = now - clock[0]
+        clock[0] = now
+
     if aggregator not in AGGREGATORS or feature not in FEATURES:
         raise ValueError("unknown aggregator or feature mode")
     xu = np.concatenate([np.asarray(xq, np.float64), np.asarray(xg, np.float64)])
@@ -211,6 +224,7 @@ def rerank(xq: np.ndarray, xg: np.ndarray, k1: int, k2: int, layers: int, alpha:
         knn_score = np.take_along_axis(s_full, knn_idx, axis=1)
     else:
         knn_idx, knn_score = knn_lists(xu, k1)                       # Eq. 7, 8
+    lap("knn")
 
     a = adjacency(knn_idx, n, dense)                                 # Eq. 8
     a_star = symmetric_adjacency(a)                                  # Eq. 9, 10
@@ -222,10 +236,13 @@ def rerank(xq: np.ndarray, xg: np.ndarray, k1: int, k2: int, layers: int, alpha:
         h0 = unit_rows(xu)
         h0 = h0 if dense else sp.csr_matrix(h0)
     w = knn_graph_weights(knn_idx, knn_score, k2, alpha, aggregator, n, dense)  # Eq. 12, 14
+    lap("graph")
     hs = [h0]
     for _ in range(layers):                                          # Eq. 13, 14
         hs.append(propagate(hs[-1], w, knn_idx, k2, aggregator))
+    lap("propagate")
     idx, dist, s = final_ranking(hs[-1], q)                          # Alg. 1 step 7
+    lap("rank")
     return OracleResult(knn_idx, knn_score, a_star, hs, idx, dist, s, s_full)
 
 

@@ -30,17 +30,25 @@ def test_stage_rooflines_bytes():
     n = nq + ng
     h_nnz = [731000, 1780000, 2540000] + [0] * 6
     st = {"normalize": 0.1, "refine": 1.0, "propagate": 0.3, "rank": 0.6, "graph": 0.09}
-    r = bench._stage_rooflines("bf16", st, nq, ng, d, k1, k2, 22, h_nnz, 2)
+    r = bench._stage_rooflines("bf16", st, nq, ng, d, k1, k2, 22, h_nnz, 2, "market")
     np_ = 23296  # rows padded to the 256-row tensor-core tile
     assert r["normalize"]["bytes"] == n * d * 4 + np_ * d * 8
-    assert r["refine"]["bytes"] == n * 32 * d * 4  # first rescoring batch: (k1 + 7) & ~3 = 32 rows
     assert r["propagate"]["bytes"] == ((k2 + 1) * 731000 + 1780000 + (k2 + 1) * 1780000 + 2540000) * 8
     assert r["rank"]["bytes"] == nq * ng * 8
     assert "graph" not in r
-    for k in ("normalize", "refine", "propagate", "rank"):
+    for k in ("normalize", "propagate", "rank"):
         v = r[k]
         assert v["achieved_gbs"] == pytest.approx(v["bytes"] / (v["ms"] * 1e-3) / 1e9)
         assert v["frac_of_hbm"] == pytest.approx(v["achieved_gbs"] / r["peak_gbs"])
+    # the refinement is a gather: its floor is every unit row read once; the
+    # first rescoring batch's rows ((k1 + 7) & ~3 = 32 per row) are a gather
+    # rate, with no HBM fraction
+    ref = r["refine"]
+    assert "frac_of_hbm" not in ref
+    assert ref["floor_bytes"] == n * d * 4
+    assert ref["floor_frac_of_hbm"] == pytest.approx(n * d * 4 / 1e-3 / 1e9 / r["peak_gbs"])
+    assert ref["gathered_bytes"] == n * 32 * d * 4
+    assert ref["gather_rate_gbs"] == pytest.approx(n * 32 * d * 4 / 1e-3 / 1e9)
     # a small rescore margin caps the first batch at k1 + m rows
-    assert bench._stage_rooflines("fp32", st, nq, ng, d, k1, k2, 2, h_nnz, 2)["refine"]["bytes"] == \
-        n * 28 * d * 4
+    assert bench._stage_rooflines("fp32", st, nq, ng, d, k1, k2, 2, h_nnz, 2, "market")["refine"][
+        "gathered_bytes"] == n * 28 * d * 4

@@ -56,7 +56,7 @@ def test_reference_arm_under_torchrun_prints_one_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
            "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"), "--impl", "reference",
-           "--workload", "tiny", "--gpus", "2", "--steps", "1", "--warmup", "0", "--cpu-seconds", "0.5"]
+           "--workload", "tiny", "--gpus", "2", "--steps", "3", "--warmup", "1", "--ref-seconds", "60"]
     r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=280, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-3000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
@@ -64,3 +64,7 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "ms" and d["higher_is_better"] is False
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    # the whole oracle ran for every step it reports (the tiny case fits the budget)
+    assert d["steps"] == 3 and d["warmup"] == 1 and d["requested"] == {"steps": 3, "warmup": 1, "budget_s": 60.0}
+    assert set(d["cpu_baseline"]["stages_ms"]) == {"knn", "graph", "propagate", "rank"}
+    assert "no scaling" in d["cpu_baseline"]["sample"]
