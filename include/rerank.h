@@ -112,7 +112,11 @@ rerank_status rerank_check_args(int64_t nq, int64_t ng, int d, int dtype, int k1
  *   out_dist  nq x topk_out float: 1 - cos(h_q, h_g) in the same order
  *   stream    cudaStream_t for the enqueued work (NULL = default stream)
  * Errors: EINVAL (as rerank_check_args, null pointers, or an input row that
- * is non-finite or has zero norm), EBUDGET, ENOMEM, ECUDA, EINTERNAL. */
+ * is non-finite or has zero norm), EBUDGET, ENOMEM, ECUDA, EINTERNAL;
+ * EUNSUPPORTED when k1 > RERANK_MAX_K1.  Each row's candidate list holds 64
+ * entries; capping k1 at 48 keeps 16 of them beyond the k1-th, so that the
+ * exact last-resort scan can always bound the columns it leaves out. */
+#define RERANK_MAX_K1 48
 rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void* xg, int64_t ng,
                          int d, int dtype, int k1, int k2, int layers, int64_t topk_out,
                          int32_t* out_idx, float* out_dist, void* stream);
@@ -313,7 +317,7 @@ rerank_status rerank_knn(rerank_ctx* ctx, const void* x, int64_t n, int d, int d
 #define RERANK_KNN_NOALLOC_SCRATCH_BYTES (13u << 20)
 #define RERANK_KNN_NOALLOC_MAX_N 4096
 #define RERANK_KNN_NOALLOC_MAX_D 256
-#define RERANK_KNN_NOALLOC_MAX_K 64
+#define RERANK_KNN_NOALLOC_MAX_K 48
 rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int dtype, int k, int32_t* out_idx,
                                  float* out_score, void* stream);
 

@@ -135,7 +135,7 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
   b.fb_rows = c.take<int32_t>(size_t(n));
   b.fb_count = c.take<int32_t>(4);
   // fallback per-warp lists (scores then indices)
-  b.scan_tmp = c.take<int64_t>(size_t(sm_count) * fallback_warps() * sh.K);
+  b.scan_tmp = c.take<int64_t>(size_t(sm_count) * fallback_warps() * std::max(sh.K, fallback_k(sh)));
   if (sh.knn_only) return c.used;
   b.indeg = c.take<int32_t>(size_t(n));
   b.fill = c.take<int32_t>(size_t(n));
@@ -346,7 +346,7 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     mark("recheck");
   }
   float* fb_s = reinterpret_cast<float*>(b.scan_tmp);
-  int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(ctx->sm_count) * fallback_warps() * sh.K);
+  int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(ctx->sm_count) * fallback_warps() * fallback_k(sh));
   nl += launch_refine_fallback(sh, dq, dg, b.xhat, b.norm, b.knn_idx, b.knn_score, exact_rows, exact_count, fb_s, fb_i,
                                status, ctx->sm_count, s);
   mark("exact_scan");
@@ -495,7 +495,7 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
   sh.host_in = host_in;
   sh.host_out = host_out;
   const int kmax = std::min(tc ? tc_kmax() : sim_fp32_kmax(), refine_kmax());
-  if (k1 > kmax) return RERANK_EUNSUPPORTED;
+  if (k1 > RERANK_MAX_K1 || k1 > kmax) return RERANK_EUNSUPPORTED;
   sh.tune = tune ? *tune : (ctx->force_tune ? *ctx->force_tune : lookup_tuning(ctx, prec, sh.n, d));
   const int m = sh.tune.rescore_m >= 0 ? sh.tune.rescore_m : ctx->cfg.rescore_m;
   int64_t K = std::min<int64_t>(int64_t(k1) + std::max(m, 0), sh.n);
@@ -506,7 +506,11 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
   // merges at most 32 lists.
   const int lpc = tc ? tc_lists_per_chunk(sh.dp, 1) : 1;
   const int lpc3 = tc ? tc_lists_per_chunk(sh.dp, 3) : 1;
-  const int chunks = choose_chunks(sh.np / 128, sh.np / (tc ? 256 : 128), ctx->sm_count, sh.tune.sim_chunks);
+  // Work items of the main pass: row blocks of tc_item_rows() rows (CTA pairs
+  // take 256) times column chunks, spread over the SMs (or SM pairs).
+  const int irows = tc ? tc_item_rows() : 128;
+  const int units = ctx->sm_count * 128 / irows;
+  const int chunks = choose_chunks(sh.np / irows, sh.np / (tc ? 256 : 128), units, sh.tune.sim_chunks);
   sh.P = std::min(chunks, 32 / lpc) * lpc;
   // The recheck covers an unknown, usually small, set of rows: many short chunks keep every SM busy.
   sh.P3 = tc ? int(std::min<int64_t>(32 / lpc3, sh.np / 256)) * lpc3 : 0;

@@ -283,10 +283,15 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
                    long long* status, cudaStream_t s, int64_t grid_rows = -1,  // grid_rows: bound on the row count
                    int fb_stat = -1);  // status slot counting the rows passed on (-1: by the row set)
 size_t tc_smem_bytes();
+bool tc_pairs();      // main similarity pass on CTA pairs (cta_group::2)
+int tc_item_rows();   // A rows per work item of the main pass: 256 on pairs, else 128
 int tc_kmax();
 // Candidate lists per row and column chunk written by the tensor-core kernels
 // (their epilogue warp groups) for K depth dp and `segs` products per k-block.
 int tc_lists_per_chunk(int dp, int segs);
+// Candidates per row kept by the exact last-resort scan: k1 + 16 (at most
+// the list capacity and n), whatever margin the first pass used.
+int fallback_k(const Shape& sh);
 int launch_refine_fallback(const Shape& sh, const void* xq, const void* xg, const float* xhat,
                             const double* norm, int32_t* knn_idx, float* knn_score,
                             const int32_t* fb_rows, const int32_t* fb_count, float* scratch_s,

@@ -32,6 +32,7 @@
 #include <climits>
 
 #include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 #include "internal.hpp"
@@ -60,18 +61,26 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2, MODE_GATHER = 3 };
 __host__ __device__ constexpr bool gathered(int mode) { return mode == MODE_SPLIT || mode == MODE_GATHER; }
 
-struct alignas(1024) TcSmem {
-  uint8_t a[STAGES][A_BYTES];
-  uint8_t b[STAGES][B_BYTES];
+// Shared memory of one CTA.  A CTA of a pair holds only its half of the B
+// rows (128 of the tile's 256), so the same space holds more stages.
+template <int STG, int BBYTES>
+struct alignas(1024) TcSmemT {
+  uint8_t a[STG][A_BYTES];
+  uint8_t b[STG][BBYTES];
   float batch[EG_MAX][32][TBM];  // per group: scores of the 32 columns being folded in
-  uint64_t full[STAGES];
-  uint64_t empty[STAGES];
+  uint64_t full[STG];
+  uint64_t empty[STG];
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t done;
   uint32_t tmem_base;
   int abort;
 };
+constexpr int PAIR_STAGES = 6;
+using TcSmem = TcSmemT<STAGES, B_BYTES>;
+using TcSmemPair = TcSmemT<PAIR_STAGES, B_BYTES / 2>;
+template <bool PAIR>
+using SmemOf = typename std::conditional<PAIR, TcSmemPair, TcSmem>::type;
 
 // Batched launches: up to kMaxBatchInst instances, each a matrix against
 // itself; their tensor maps travel as one kernel parameter.
@@ -207,27 +216,47 @@ __device__ void report_timeout(const TcArgs& A) {
 
 
 
-template <int MODE, int KL, int EGROUPS, bool BATCH>
+// Give loads this CTA issued time to land before it leaves (pair mode, after a
+// timeout: their bytes complete on the even CTA's barrier, which this CTA
+// cannot poll).  A tile load takes microseconds; wait about 200 us.
+__device__ __forceinline__ void drain_delay() {
+  for (int k = 0; k < 200; ++k) __nanosleep(1000);
+}
+
+// PAIR: the CTAs of a cluster of two compute 256-row tiles together with
+// tcgen05 cta_group::2.  The even CTA ("leader") issues the MMAs; each CTA
+// loads its own 128 rows of A and its 128 of the tile's 256 B rows, counted
+// on the leader's `full` barrier; the MMA's commits reach both CTAs'
+// `empty` / `tfull` barriers; both CTAs' epilogue warps release an
+// accumulator on the leader's `tempty`.
+template <int MODE, int KL, int EGROUPS, bool BATCH, bool PAIR>
 __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMap* pA1, const CUtensorMap* pB0,
                                         const CUtensorMap* pB1, const CUtensorMap* bmaps, const TcArgs& A) {
+  using Smem = SmemOf<PAIR>;
+  constexpr int STG = PAIR ? PAIR_STAGES : STAGES;
+  constexpr int ROWS = PAIR ? 2 * TBM : TBM;  // A rows of one work item
   extern __shared__ uint8_t smem_raw[];
-  TcSmem& sm = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort = &sm.abort;
   constexpr int SEGS = MODE == MODE_SPLIT ? 3 : 1;
+  const uint32_t rank = PAIR ? tc::cluster_rank() : 0u;
+  const bool leader = rank == 0;
+  const int unit = PAIR ? int(blockIdx.x >> 1) : int(blockIdx.x);   // cluster (pair) or CTA
+  const int units = PAIR ? int(gridDim.x >> 1) : int(gridDim.x);
   const int64_t nrows = gathered(MODE) ? int64_t(*A.count) : A.a_rows;
   const int row_blocks = gathered(MODE) ? int((nrows + TBM - 1) / TBM) : A.row_blocks;
-  const int chunks = gathered(MODE) ? pick_chunks(row_blocks, A.chunks, A.col_tiles, int(gridDim.x)) : A.chunks;
+  const int chunks = gathered(MODE) ? pick_chunks(row_blocks, A.chunks, A.col_tiles, units) : A.chunks;
   const int items = BATCH ? A.items_total : row_blocks * chunks;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      tc::mbar_init(&sm.full[s], 1);
-      tc::mbar_init(&sm.empty[s], 1);
+    for (int st = 0; st < STG; ++st) {
+      tc::mbar_init(&sm.full[st], 1);
+      tc::mbar_init(&sm.empty[st], 1);
     }
     for (int b = 0; b < 2; ++b) {
       tc::mbar_init(&sm.tfull[b], 1);
-      tc::mbar_init(&sm.tempty[b], 4 * EGROUPS);
+      tc::mbar_init(&sm.tempty[b], 4 * EGROUPS * (PAIR ? 2 : 1));
     }
     tc::mbar_init(&sm.done, 1);
     sm.abort = 0;
@@ -242,11 +271,17 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
     }
   }
   if (warp == 1) {
-    tc::tmem_alloc(&sm.tmem_base, 512);
-    tc::tmem_relinquish();
+    if (PAIR) {
+      tc::tmem_alloc_pair(&sm.tmem_base, 512);
+      tc::tmem_relinquish_pair();
+    } else {
+      tc::tmem_alloc(&sm.tmem_base, 512);
+      tc::tmem_relinquish();
+    }
   }
   tc::tc_fence_before();
   __syncthreads();
+  if (PAIR) tc::cluster_sync();  // the peer's barriers are initialised before any cross-CTA signal
   tc::tc_fence_after();
   const uint32_t tmem = sm.tmem_base;
 
@@ -257,7 +292,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
       uint32_t armed = 0;  // bit s: slot s holds a load that may still be in flight
       uint32_t armed_phase = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < items && ok && !A.stall; item += gridDim.x) {
+      for (int item = unit; item < items && ok && !A.stall; item += units) {
         TcItem it;
         get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
         const int rb = it.rb;
@@ -271,14 +306,22 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
             const int seg = kt / it.kblocks, kb = kt - seg * it.kblocks;
             const CUtensorMap* ma = seg == 1 ? it.ma1 : it.ma0;
             const CUtensorMap* mb = seg == 2 ? it.mb1 : it.mb0;
-            tc::mbar_arrive_expect_tx(&sm.full[stage], A_BYTES + B_BYTES);
             const int kx = kb * (MODE == MODE_FP8 ? 128 : 64);
-            tc::tma_load_2d(sm.a[stage], ma, &sm.full[stage], kx, rb * TBM);
-            tc::tma_load_2d(sm.b[stage], mb, &sm.full[stage], kx, ct * TBN);
-            tc::tma_load_2d(sm.b[stage] + B_BYTES / 2, mb, &sm.full[stage], kx, ct * TBN + TBN / 2);
+            if (PAIR) {
+              // this CTA's A rows and its half of the tile's B rows; bytes counted on the leader
+              const uint32_t bar = tc::map_to_rank(&sm.full[stage], 0);
+              if (leader) tc::mbar_arrive_expect_tx(&sm.full[stage], 2 * (A_BYTES + B_BYTES / 2));
+              tc::tma_load_2d_pair(sm.a[stage], ma, bar, kx, rb * ROWS + int(rank) * TBM);
+              tc::tma_load_2d_pair(sm.b[stage], mb, bar, kx, ct * TBN + int(rank) * (TBN / 2));
+            } else {
+              tc::mbar_arrive_expect_tx(&sm.full[stage], A_BYTES + B_BYTES);
+              tc::tma_load_2d(sm.a[stage], ma, &sm.full[stage], kx, rb * TBM);
+              tc::tma_load_2d(sm.b[stage], mb, &sm.full[stage], kx, ct * TBN);
+              tc::tma_load_2d(sm.b[stage] + B_BYTES / 2, mb, &sm.full[stage], kx, ct * TBN + TBN / 2);
+            }
             armed |= 1u << stage;
             armed_phase = (armed_phase & ~(1u << stage)) | (phase << stage);
-            if (++stage == STAGES) {
+            if (++stage == STG) {
               stage = 0;
               phase ^= 1u;
             }
@@ -289,17 +332,22 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
         *abort = 1;
         report_timeout<BATCH>(A);
         // Let loads already issued land before the CTA exits.
-        for (int s = 0; s < STAGES; ++s)
-          if (armed & (1u << s)) tc::mbar_wait(&sm.full[s], (armed_phase >> s) & 1u, abort, WAIT_LIMIT);
+        if (PAIR && !leader) {
+          if (armed) drain_delay();
+        } else {
+          for (int st = 0; st < STG; ++st)
+            if (armed & (1u << st)) tc::mbar_wait(&sm.full[st], (armed_phase >> st) & 1u, abort, WAIT_LIMIT);
+        }
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = tc::instr_desc(MODE == MODE_FP8 ? 0u : 1u, TBM, TBN);
+    if (lane == 0 && leader) {
+      // ---------------- MMA issuer (the leader of a pair) ----------------
+      constexpr uint32_t idesc = tc::instr_desc(MODE == MODE_FP8 ? 0u : 1u, ROWS, TBN);
+      constexpr uint16_t both = 3;
       uint32_t stage = 0, phase = 0, tcount = 0;
       bool ok = true;
-      for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+      for (int item = unit; item < items && ok; item += units) {
         TcItem it;
         get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
         const int kb_total = it.kblocks * SEGS;
@@ -322,19 +370,25 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
               // 32 bytes of K per instruction: advance the start address by 2 (16-byte units).
-              if (MODE == MODE_FP8)
-                tc::mma_fp8(d, da + 2u * kk, db + 2u * kk, idesc, (kt | kk) != 0);
-              else
-                tc::mma_bf16(d, da + 2u * kk, db + 2u * kk, idesc, (kt | kk) != 0);
+              const uint32_t acc = (kt | kk) != 0;
+              if (PAIR) {
+                if (MODE == MODE_FP8) tc::mma_fp8_pair(d, da + 2u * kk, db + 2u * kk, idesc, acc);
+                else tc::mma_bf16_pair(d, da + 2u * kk, db + 2u * kk, idesc, acc);
+              } else {
+                if (MODE == MODE_FP8) tc::mma_fp8(d, da + 2u * kk, db + 2u * kk, idesc, acc);
+                else tc::mma_bf16(d, da + 2u * kk, db + 2u * kk, idesc, acc);
+              }
             }
-            tc::mma_commit(&sm.empty[stage]);
-            if (++stage == STAGES) {
+            if (PAIR) tc::mma_commit_pair(&sm.empty[stage], both);
+            else tc::mma_commit(&sm.empty[stage]);
+            if (++stage == STG) {
               stage = 0;
               phase ^= 1u;
             }
           }
           if (!ok) break;
-          tc::mma_commit(&sm.tfull[ab]);
+          if (PAIR) tc::mma_commit_pair(&sm.tfull[ab], both);
+          else tc::mma_commit(&sm.tfull[ab]);
           ++tcount;
         }
       }
@@ -343,7 +397,8 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
         report_timeout<BATCH>(A);
       }
       // Every MMA issued by this thread has completed once `done` fires.
-      tc::mma_commit(&sm.done);
+      if (PAIR) tc::mma_commit_pair(&sm.done, 1);
+      else tc::mma_commit(&sm.done);
       tc::mbar_wait(&sm.done, 0, abort, WAIT_LIMIT);
     }
   } else {
@@ -354,6 +409,8 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
     const int eg = (warp - 2) >> 2;
     const int r = q * 32 + lane;
     const uint32_t tlane = tmem + (uint32_t(q * 32) << 16);
+    const uint32_t tempty_leader0 = PAIR ? tc::map_to_rank(&sm.tempty[0], 0) : 0u;
+    const uint32_t tempty_leader1 = PAIR ? tc::map_to_rank(&sm.tempty[1], 0) : 0u;
     uint32_t tcount = 0;
     bool ok = true;
     // This row's best KL columns of the current chunk: scores ls (descending)
@@ -362,11 +419,11 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
     // score keeps the earlier, lower column in front (score desc, column asc).
     float ls[KL];
     int li[KL];
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+    for (int item = unit; item < items && ok; item += units) {
       TcItem it;
       get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
       const int chunk = it.chunk;
-      const int64_t arow = int64_t(it.rb) * TBM + r;   // row of the A operand
+      const int64_t arow = int64_t(it.rb) * ROWS + int(rank) * TBM + r;   // row of the A operand
       const bool live = arow < it.nrows;
       const int64_t grow = gathered(MODE) ? (live ? int64_t(A.rows[arow]) : -1) : it.row0 + arow;  // vertex
 #pragma unroll
@@ -402,12 +459,12 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
           uint32_t mask = 0;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            float s = __uint_as_float(v[j]);
-            if (MODE == MODE_FP8) s = s * rinv * __ldg(it.inv_scale + (j < nvalid ? cbase + j : 0));
-            if (j == jself) s = 1.0f;
-            if (j >= nvalid) s = -INFINITY;
-            sm.batch[eg][j][r] = s;
-            mask |= (s > thr) ? (1u << j) : 0u;
+            float sc = __uint_as_float(v[j]);
+            if (MODE == MODE_FP8) sc = sc * rinv * __ldg(it.inv_scale + (j < nvalid ? cbase + j : 0));
+            if (j == jself) sc = 1.0f;
+            if (j >= nvalid) sc = -INFINITY;
+            sm.batch[eg][j][r] = sc;
+            mask |= (sc > thr) ? (1u << j) : 0u;
           }
           int rounds = __popc(mask);
 #pragma unroll
@@ -438,7 +495,10 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
         }
         tc::tc_fence_before();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&sm.tempty[ab]);
+        if (lane == 0) {
+          if (PAIR && !leader) tc::mbar_arrive_cluster(ab ? tempty_leader1 : tempty_leader0);
+          else tc::mbar_arrive(&sm.tempty[ab]);
+        }
         ++tcount;
       }
       if (!ok) break;
@@ -474,15 +534,27 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
 
   tc::tc_fence_before();
   __syncthreads();
+  if (PAIR) tc::cluster_sync();  // neither CTA leaves while the pair's MMAs or signals may touch it
   tc::tc_fence_after();
-  if (warp == 1) tc::tmem_dealloc(tmem, 512);
+  if (warp == 1) {
+    if (PAIR) tc::tmem_dealloc_pair(tmem, 512);
+    else tc::tmem_dealloc(tmem, 512);
+  }
 }
 
 template <int MODE, int KL, int EGROUPS>
 __global__ void __launch_bounds__(threads_of(EGROUPS), 1)
 k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
            const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs A) {
-  tc_body<MODE, KL, EGROUPS, false>(&mA0, &mA1, &mB0, &mB1, nullptr, A);
+  tc_body<MODE, KL, EGROUPS, false, false>(&mA0, &mA1, &mB0, &mB1, nullptr, A);
+}
+
+// CTA pairs (launched in clusters of two): 256-row items, one cta_group::2
+// MMA per k-step for both SMs.
+template <int MODE, int KL, int EGROUPS>
+__global__ void __launch_bounds__(threads_of(EGROUPS), 1)
+k1_tc2_topk(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, TcArgs A) {
+  tc_body<MODE, KL, EGROUPS, false, true>(&mA, &mA, &mB, &mB, nullptr, A);
 }
 
 // Many instances in one persistent launch: the items of all instances form one
@@ -490,7 +562,7 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
 template <int MODE, int KL, int EGROUPS>
 __global__ void __launch_bounds__(threads_of(EGROUPS), 1)
 k1_tc_topk_batch(const __grid_constant__ TcMaps maps, TcArgs A) {
-  tc_body<MODE, KL, EGROUPS, true>(nullptr, nullptr, nullptr, nullptr, maps.m, A);
+  tc_body<MODE, KL, EGROUPS, true, false>(nullptr, nullptr, nullptr, nullptr, maps.m, A);
 }
 
 // Test hook: RERANK_TEST_TC_STALL set in the environment makes the kernels'
@@ -535,6 +607,66 @@ void launch_kl(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& 
   k1_tc_topk<MODE, KL, EG><<<grid, threads_of(EG), smem, s>>>(a0, a1, b0, b1, A);
 }
 
+// Pairs that can be resident at once (clusters of two, one CTA per SM); 0 if
+// the query fails.
+template <int MODE, int KL, int EG>
+int pair_units(int sm_count) {
+  static int cached = -1;
+  if (cached < 0) {
+    const size_t smem = sizeof(TcSmemPair) + 1024;
+    cudaFuncSetAttribute(k1_tc2_topk<MODE, KL, EG>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(unsigned(sm_count & ~1));
+    cfg.blockDim = dim3(threads_of(EG));
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k1_tc2_topk<MODE, KL, EG>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    cached = n;
+  }
+  return cached;
+}
+
+template <int MODE, int KL, int EG>
+bool launch_kl_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A, int items, int sm_count,
+                    cudaStream_t s) {
+  const int units = pair_units<MODE, KL, EG>(sm_count);
+  if (units < 1) return false;
+  const size_t smem = sizeof(TcSmemPair) + 1024;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(unsigned(2 * (items < units ? items : units)));
+  cfg.blockDim = dim3(threads_of(EG));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k1_tc2_topk<MODE, KL, EG>, a, b, A) == cudaSuccess;
+}
+
+template <int MODE>
+bool launch_mode_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A, int eg, int items, int sm_count,
+                      cudaStream_t s) {
+  if (A.K <= 48)
+    return eg == 2 ? launch_kl_pair<MODE, 48, 2>(a, b, A, items, sm_count, s)
+                   : launch_kl_pair<MODE, 48, 1>(a, b, A, items, sm_count, s);
+  return eg == 2 ? launch_kl_pair<MODE, KLIST, 2>(a, b, A, items, sm_count, s)
+                 : launch_kl_pair<MODE, KLIST, 1>(a, b, A, items, sm_count, s);
+}
+
 // The per-row list lives in registers, so its length is a compile-time choice.
 template <int MODE>
 void launch_mode(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
@@ -568,6 +700,17 @@ __global__ void k_gather_rows(const int32_t* __restrict__ rows, const int32_t* _
 }  // namespace
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
+static_assert(sizeof(TcSmemPair) + 1024 <= 227 * 1024, "shared memory of the paired tensor-core kernel");
+// Whether the main similarity pass runs on CTA pairs (cta_group::2).  Both
+// kernels give identical lists; RERANK_TC_PAIRS=0 selects the single-CTA one.
+bool tc_pairs() {
+  static const int on = [] {
+    const char* e = std::getenv("RERANK_TC_PAIRS");
+    return (e && e[0] == '0') ? 0 : 1;
+  }();
+  return on != 0;
+}
+int tc_item_rows() { return tc_pairs() ? 2 * TBM : TBM; }
 int tc_lists_per_chunk(int dp, int segs) { return dp * segs <= 1024 ? 2 : 1; }
 static_assert(sizeof(TcSmem) + 1024 <= 227 * 1024, "shared memory of the tensor-core kernel");
 int tc_kmax() { return KLIST; }
@@ -581,10 +724,11 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   CUtensorMap map;
   if (!make_map(&map, xlow, sh.np, sh.dp, fp8)) return -1;
   cudaMemsetAsync(row_floor, kFloorResetByte, sizeof(int) * size_t(sh.n), s);
+  const bool pairs = tc_pairs() && sm_count >= 2 && sh.np % (2 * TBM) == 0;
   TcArgs A{};
   A.n = sh.n;
   A.a_rows = sh.n;
-  A.row_blocks = int(sh.np / TBM);
+  A.row_blocks = int(sh.np / (pairs ? 2 * TBM : TBM));
   A.col_tiles = int(sh.np / TBN);
   const int eg = tc_lists_per_chunk(sh.dp, 1);
   A.chunks = sh.P / eg;  // sh.P counts lists per row
@@ -598,6 +742,11 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   A.status = status;
   A.stall = stall_hook();
   const int items = A.row_blocks * A.chunks;
+  if (pairs) {
+    const bool ok = fp8 ? launch_mode_pair<MODE_FP8>(map, map, A, eg, items, sm_count, s)
+                        : launch_mode_pair<MODE_BF16>(map, map, A, eg, items, sm_count, s);
+    return ok ? 1 : -1;
+  }
   const int grid = items < sm_count ? items : sm_count;
   if (fp8)
     launch_mode<MODE_FP8>(map, map, map, map, A, eg, grid, s);

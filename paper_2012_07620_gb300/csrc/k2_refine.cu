@@ -20,6 +20,7 @@
 //      Outside such runs the FP32 order is already the exact order.
 // Output: knn_idx[i][0..k1) and knn_score (the FP64 value where one was
 // computed, else s).  Self gets S_ii = 1 exactly.
+#include <algorithm>
 #include <cfloat>
 
 #include "common.cuh"
@@ -511,12 +512,16 @@ int launch_refine_fallback(const Shape& sh, const void* xq, const void* xg, cons
                             const int32_t* fb_count, float* scratch_s, int32_t* scratch_i, long long* status,
                             int sm_count, cudaStream_t s) {
   RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
-  k2_fallback<<<sm_count, FB_WARPS * kWarp, 0, s>>>(io, sh.n, sh.K, sh.k1, rescore_eps(sh.dp), fb_rows, fb_count,
-                                                    scratch_s, scratch_i);
+  k2_fallback<<<sm_count, FB_WARPS * kWarp, 0, s>>>(io, sh.n, fallback_k(sh), sh.k1, rescore_eps(sh.dp), fb_rows,
+                                                    fb_count, scratch_s, scratch_i);
   return 1;
 }
 
 int refine_kmax() { return KMAX; }
+int fallback_k(const Shape& sh) {
+  const int64_t k = std::min<int64_t>(std::min<int64_t>(int64_t(sh.k1) + 16, sh.n), KMAX);
+  return int(k);
+}
 int fallback_warps() { return FB_WARPS; }
 
 }  // namespace rr

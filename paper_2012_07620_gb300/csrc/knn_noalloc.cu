@@ -19,7 +19,8 @@ namespace {
 
 constexpr int64_t kMaxN = RERANK_KNN_NOALLOC_MAX_N;
 constexpr int kMaxD = RERANK_KNN_NOALLOC_MAX_D;
-constexpr int kMaxK = RERANK_KNN_NOALLOC_MAX_K;
+constexpr int kMaxK = 64;  // candidate list capacity (k + 16 for the largest k)
+static_assert(RERANK_KNN_NOALLOC_MAX_K + 16 <= kMaxK, "candidate lists of the largest k");
 constexpr int kChunks = 4;      // column chunks of the similarity kernel
 constexpr int kFbCtas = 16;     // CTAs of the exact fallback kernel
 constexpr int kFbWarps = 32;    // warps per fallback CTA (as the fallback kernel uses)
@@ -91,7 +92,7 @@ extern "C" rerank_status rerank_knn_noalloc(const void* x, int64_t n, int d, int
   if (!x || !out_idx || !out_score) return RERANK_EINVAL;
   if (n < 1 || d < 1 || k < 1 || k > n || (dtype != RERANK_DTYPE_F32 && dtype != RERANK_DTYPE_BF16))
     return RERANK_EINVAL;
-  if (n > kMaxN || d > kMaxD || k > kMaxK) return RERANK_EBUDGET;
+  if (n > kMaxN || d > kMaxD || k > RERANK_KNN_NOALLOC_MAX_K) return RERANK_EBUDGET;
   int dev = 0;
   RR_CUDA(cudaGetDevice(&dev));
   if (!on_device(x, dev) || !on_device(out_idx, dev) || !on_device(out_score, dev)) return RERANK_EINVAL;

@@ -491,7 +491,7 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3, e3, b.fb_rows, b.fb_count, false, b.knn_idx,
                 b.knn_score, b.fb2_rows, b.fb2_count, status, s);
   float* fb_s = reinterpret_cast<float*>(b.scan_tmp);
-  int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(sm) * fallback_warps() * sh.K);
+  int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(sm) * fallback_warps() * fallback_k(sh));
   launch_refine_fallback(sh, dq, dg, b.xhat, b.norm, b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, fb_s, fb_i,
                          status, sm, s);
   // 5. graph, propagation, ranking on X_u

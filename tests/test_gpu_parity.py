@@ -110,7 +110,8 @@ def test_clustered_shapes(R, nq, ng, d, c, k1, k2, layers):
     (1, 700, 96, 20, 5, 3, 0),      # one query
     (50, 1, 64, 26, 7, 2, 0),       # one gallery item
     (40, 200, 32, 1, 1, 0, 0),      # k1 = k2 = 1, no layers
-    (20, 44, 48, 64, 1, 2, 0),      # k1 = n = 64 (every vertex a neighbour)
+    (20, 28, 48, 48, 1, 2, 0),      # k1 = n = 48 = RERANK_MAX_K1 (every vertex a neighbour)
+    (30, 970, 40, 48, 7, 1, 0),     # k1 = RERANK_MAX_K1 with n >> k1
     (30, 500, 128, 26, 7, 0, 0),    # no propagation
     (64, 900, 128, 26, 7, 2, 17),   # truncated output lists
     (5, 1000, 16, 8, 8, 4, 0),      # k2 = k1, four layers
@@ -256,3 +257,21 @@ def test_rank_sort_paths_agree():
         assert r.returncode == 0 and "digest" in r.stdout, (caps, r.stderr[-2000:])
         digests.append(r.stdout.split("digest")[-1].strip())
     assert len(set(digests)) == 1, digests
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_no_rescore_margin_sends_rows_to_the_exact_scan(precision):
+    """With rescore_m = 0 the first pass keeps exactly k1 candidates, so no
+    list can be certified (Eq. 8's boundary is unbounded) and every row goes
+    on to the exact scan, which keeps k1 + 16 candidates of its own; at
+    k1 = RERANK_MAX_K1 = 48 the lists must still equal the oracle's."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2012_07620_gb300 import rerank
+    spec = synthetic.WorkloadSpec("nomargin", 60, 1140, 64, 70, 0.35, 100, None, seed=91)
+    w = synthetic.make_workload(spec)
+    with rerank.Reranker(device=0, precision=precision, rescore_m=0) as R:
+        stats = _check_all(R, w.xq, w.xg, 48, 7, 2)
+        info = R.last_info()
+    assert info["exact_scan_rows"] > 0 or info["fallback_rows"] > 0
+    assert stats["max_dist_err"] < 1e-5

@@ -6,7 +6,7 @@ wait for an allocation, or under a fixed memory footprint.  For them the
 library offers rerank_knn_noalloc, which keeps its temporaries in a fixed
 scratch area compiled into the library.  These tests call it through the C
 ABI on several calls in a row that share that scratch area (the limit
-corner n = 4096, d = 256, k = 64 among them, then smaller calls, so that
+corner n = 4096, d = 256, k = 48 among them, then smaller calls, so that
 leftovers of an earlier call would show), compare every call with the
 allocating entry point rerank_knn, and compare one call directly with the
 FP64 oracle's neighbour lists (Eq. 7-8).  They also check that sizes over
@@ -40,11 +40,11 @@ def _entry():
     return fn, rerank
 
 
-# (n, d, k, dtype): an ordinary call, the limit corner (the scratch layout is
-# full and K = k leaves no rescoring margin, so rows go to the exact scan),
+# (n, d, k, dtype): an ordinary call, the limit corner (n, d and k at their
+# maxima: the scratch layout is full and the candidate lists are full length),
 # BF16 input with a width that is not a multiple of 4 (the scalar
 # normalisation path), and a small call after the big ones.
-CALLS = [(4000, 256, 30, "f32"), (4096, 256, 64, "f32"), (1500, 130, 20, "bf16"), (700, 64, 12, "f32")]
+CALLS = [(4000, 256, 30, "f32"), (4096, 256, 48, "f32"), (1500, 130, 20, "bf16"), (700, 64, 12, "f32")]
 
 
 def _score_bound(d):
@@ -87,6 +87,7 @@ def test_noalloc_refuses_sizes_over_the_limits_and_host_buffers():
     assert fn(x.data_ptr(), 5000, 8, 0, 10, idx.data_ptr(), score.data_ptr(), stream) == EBUDGET   # n
     assert fn(x.data_ptr(), 100, 300, 0, 10, idx.data_ptr(), score.data_ptr(), stream) == EBUDGET  # d
     assert fn(x.data_ptr(), 100, 8, 0, 80, idx.data_ptr(), score.data_ptr(), stream) == EBUDGET    # k
+    assert fn(x.data_ptr(), 100, 8, 0, 49, idx.data_ptr(), score.data_ptr(), stream) == EBUDGET    # k = max + 1
     # a pageable host array is refused before anything runs
     hx = np.ones((100, 8), dtype=np.float32)
     assert fn(hx.ctypes.data, 100, 8, 0, 10, idx.data_ptr(), score.data_ptr(), stream) == EINVAL
