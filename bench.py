@@ -143,13 +143,21 @@ def _max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
+# Arm "CPU part" numbers of the cores this may run on (from Arm's published part list).
+_ARM_PARTS = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1", "0xd49": "Neoverse-N2",
+              "0xd83": "Neoverse-V3"}
+
+
 def _cpu_model():
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 low = line.lower()
-                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                if low.startswith("model name"):
                     return line.split(":", 1)[1].strip()
+                if low.startswith("cpu part"):
+                    part = line.split(":", 1)[1].strip().lower()
+                    return f"Arm {_ARM_PARTS.get(part, 'core')} (CPU part {part})"
     except OSError:
         pass
     import platform
