@@ -70,8 +70,9 @@ typedef struct {
   float alpha;               /* exponent of Eq. 14; default 2 */
   int aggregator;            /* RERANK_AGG_*; default SUM (Sec. 4.1); MEAN divides the k2 messages'
                                 weights by k2; MAX takes their element-wise max (Eq. 13 variants) */
-  int feature_mode;          /* RERANK_FEAT_*; default ASTAR; X (dense x_i features) makes
-                                rerank_run / rerank_run_batch return EUNSUPPORTED */
+  int feature_mode;          /* RERANK_FEAT_*; default ASTAR.  X: h^(0) = x_i / ||x_i|| (dense
+                                d-dimensional rows), propagated densely, final cosines over d;
+                                rerank_run only (rerank_run_batch and serving return EUNSUPPORTED) */
   size_t hbm_budget;         /* workspace cap in bytes; 0 = no cap */
   const char* autotune_path; /* JSON tuning table to read (and to write from rerank_autotune); NULL = built-in */
   int stage_timing;          /* nonzero: record CUDA events around every stage (rerank_stage_times) */
@@ -358,7 +359,9 @@ enum {
   RERANK_DBG_HL_VAL = 8,     /* capacity float */
   RERANK_DBG_PART_S = 9,     /* n x P x K float: per-chunk candidate scores of the similarity kernel */
   RERANK_DBG_PART_I = 10,    /* n x P x K int32: their column indices (0x7fffffff = empty slot) */
-  RERANK_DBG_QERR = 11       /* n_pad float: per-row bound on ||unit row - its BF16/FP8 copy|| (tensor-core path) */
+  RERANK_DBG_QERR = 11,      /* n_pad float: per-row bound on ||unit row - its BF16/FP8 copy|| (tensor-core path) */
+  RERANK_DBG_HL_DENSE = 12   /* n x d_p float (d_p = d rounded up to 64, zero padded): h^(L) of a
+                                RERANK_FEAT_X run */
 };
 rerank_status rerank_debug_copy(const rerank_ctx* ctx, int what, void* dst, size_t cap,
                                 size_t* bytes);

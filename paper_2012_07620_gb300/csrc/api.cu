@@ -165,6 +165,12 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
   b.csc_row = c.take<int32_t>(size_t(sh.cap_h));
   b.csc_val = c.take<float>(size_t(sh.cap_h));
   b.rank_scratch = c.take<uint32_t>(size_t(sh.rank_ctas) * size_t(rank_scratch_words(sh.ng)));
+  if (sh.dense) {
+    b.hd[0] = c.take<float>(size_t(np) * sh.dp);
+    b.hd[1] = c.take<float>(size_t(np) * sh.dp);
+    b.hinv = c.take<double>(size_t(np));
+    b.xscore = c.take<float>(size_t(sh.nq) * size_t(sh.ng));
+  }
   return c.used;
 }
 
@@ -364,6 +370,30 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     nl += launch_graph(sh, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, status, s);
     RR_CUDA(cudaGetLastError());
     mark("graph");
+    if (sh.dense) {
+      // h^(0) = the unit rows x_i / ||x_i||; L dense layers; cosines over d; ranking.
+      const float* h = b.xhat;
+      for (int l = 0; l < sh.layers; ++l) {
+        nl += launch_dense_layer(sh, h, b.hd[l & 1], b.nbr, b.nbr_w, b.nbr_n, ctx->cfg.aggregator, s);
+        h = b.hd[l & 1];
+      }
+      RR_CUDA(cudaGetLastError());
+      mark("propagate");
+      int32_t* oi = sh.host_out ? b.out_idx : j.out_idx;
+      float* od = sh.host_out ? b.out_dist : j.out_dist;
+      nl += launch_dense_scores(sh, h, b.hinv, b.xscore, s);
+      nl += launch_rank_dense(sh, b.xscore, oi, od, b.rank_scratch, status, s);
+      RR_CUDA(cudaGetLastError());
+      mark("rank");
+      if (sh.host_out) {
+        const size_t cnt = size_t(sh.nq) * sh.topk;
+        RR_CUDA(cudaMemcpyAsync(j.out_idx, b.out_idx, cnt * 4, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaMemcpyAsync(j.out_dist, b.out_dist, cnt * 4, cudaMemcpyDeviceToHost, s));
+        mark("d2h");
+      }
+      *launches += nl;
+      return RERANK_OK;
+    }
     RR_CUDA(cudaMemsetAsync(b.hash_keys_vals, 0,
                             sizeof(float) * size_t(ctx->sm_count) * (size_t(sh.n) + size_t((sh.n + 31) / 32)), s));
     int src = 2;
@@ -520,6 +550,8 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
   int64_t guess = std::max<int64_t>(2 * sh.n * k1, std::min<int64_t>(sh.n * sh.n, sh.n * int64_t(k2 + 1) * 160));
   if (ctx->test_cap_h > 0) guess = ctx->test_cap_h;
   sh.cap_h = std::max<int64_t>(guess, cap_hint);
+  sh.dense = !knn_only && ctx->cfg.feature_mode == RERANK_FEAT_X;
+  if (sh.dense) sh.cap_h = 1;  // the sparse layer buffers are not used
   sh.rank_ctas = ctx->sm_count;
   if (sh.n * int64_t(k1) >= (int64_t(1) << 31) || sh.n >= (int64_t(1) << 31) - 1) return RERANK_EUNSUPPORTED;
   *out = sh;
@@ -1035,7 +1067,6 @@ rerank_status rerank_run(rerank_ctx* ctx, const void* xq, int64_t nq, const void
   if (!ctx || !xq || !xg || !out_idx || !out_dist) return RERANK_EINVAL;
   rerank_status st = rerank_check_args(nq, ng, d, dtype, k1, k2, layers, topk_out);
   if (st != RERANK_OK) return st;
-  if (ctx->cfg.feature_mode == RERANK_FEAT_X) return RERANK_EUNSUPPORTED;
   RR_CUDA(cudaSetDevice(ctx->device));
   const bool host_in = is_host_ptr(xq) || is_host_ptr(xg);
   const bool host_out = is_host_ptr(out_idx) || is_host_ptr(out_dist);
@@ -1112,6 +1143,11 @@ rerank_status rerank_debug_copy(const rerank_ctx* ctx, int what, void* dst, size
     case RERANK_DBG_PART_S: src = b.part_s; nb = size_t(sh.n) * sh.P * sh.K * 4; break;
     case RERANK_DBG_PART_I: src = b.part_i; nb = size_t(sh.n) * sh.P * sh.K * 4; break;
     case RERANK_DBG_QERR: src = b.err; nb = size_t(sh.np) * 4; break;
+    case RERANK_DBG_HL_DENSE:
+      if (!sh.dense) return RERANK_EINVAL;
+      src = sh.layers == 0 ? b.xhat : b.hd[(sh.layers - 1) & 1];
+      nb = size_t(sh.n) * sh.dp * 4;
+      break;
     default: return RERANK_EINVAL;
   }
   if (sh.knn_only && what > RERANK_DBG_KNN_SCORE && what < RERANK_DBG_PART_S) return RERANK_EINVAL;

@@ -119,6 +119,10 @@ struct Buffers {
   int32_t* csc_row = nullptr;
   float* csc_val = nullptr;
   uint32_t* rank_scratch = nullptr;
+  // dense features (RERANK_FEAT_X)
+  float* hd[2] = {nullptr, nullptr};  // np x dp each, alternating layers
+  double* hinv = nullptr;             // np: 1 / ||h_i^(L)||
+  float* xscore = nullptr;            // nq x ng final cosines
   // scan scratch
   int64_t* scan_tmp = nullptr;
 };
@@ -133,6 +137,7 @@ struct Shape {
   bool host_in = false, host_out = false;
   bool knn_only = false;
   bool ext_feat = false;   // the unit rows and their copies live outside the workspace (serving)
+  bool dense = false;      // h^(0) = x_i: dense layers and final cosines (RERANK_FEAT_X)
   int64_t cap_h = 0;       // elements per padded-CSR layer buffer
   int64_t cap_csc = 0;
   int hash_slots = 0;      // slots of each global hash table (big-row path)
@@ -347,6 +352,16 @@ int launch_rank_prep(const Shape& sh, const Buffers& b, int src, long long* stat
 int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out_idx, float* out_dist, int64_t q0,
                         int64_t q1, long long* status, int sm_count, const Tuning& t, cudaStream_t s,
                         const RankReuse* reuse = nullptr);
+
+// Dense initial features (RERANK_FEAT_X): one propagation layer hin -> hout
+// (np x dp rows, Eq. 13-14 with the graph's message lists), the final cosines
+// of every query row with every gallery row into S (nq x ng), and their
+// ranking (one query per CTA, sort scratch rank_scratch_words(ng) per CTA).
+int launch_dense_layer(const Shape& sh, const float* hin, float* hout, const int32_t* nbr, const float* nbr_w,
+                       const int32_t* nbr_n, int aggregator, cudaStream_t s);
+int launch_dense_scores(const Shape& sh, const float* h, double* inv, float* S, cudaStream_t s);
+int launch_rank_dense(const Shape& sh, const float* S, int32_t* out_idx, float* out_dist, uint32_t* scratch,
+                      long long* status, cudaStream_t s);
 
 size_t rank_smem_bytes(int64_t ng, int threads);
 // 32-bit words of global scratch per ranking CTA for a gallery of ng.

@@ -22,6 +22,7 @@
 // computed, else s).  Self gets S_ii = 1 exactly.
 #include <algorithm>
 #include <cfloat>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "internal.hpp"
@@ -358,18 +359,8 @@ __device__ bool refine_warp(WarpSmem& w, int Kc, int64_t i, int k1, float B, dou
   return ok;
 }
 
-template <int RV>
-__global__ void __launch_bounds__(WPB * kWarp)
-k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* __restrict__ part_i, int P,
-          int K, int k1, ErrModel em, double eps_r, const int32_t* __restrict__ rows,
-          const int32_t* __restrict__ count, bool part_by_row, int32_t* fb_rows, int32_t* fb_count,
-          int fb_stat) {
-  __shared__ WarpSmem sm[WPB];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t f = int64_t(blockIdx.x) * WPB + wib;  // position of the row in this launch's row set
-  if (f >= ((rows && count) ? int64_t(*count) : n)) return;
-  const int64_t i = rows ? int64_t(rows[f]) : f;
-  // Bound on |approximate score - S_ij| for this row and any column j (unit rows).
+// Bound on |approximate score - S_ij| for row i and any column j (unit rows).
+__device__ __forceinline__ double row_eps_g(const ErrModel& em, int64_t i) {
   double eps_g = em.eps;
   if (em.kind == 1) {
     // one quantised copy q = x - e:  |<q_i,q_j> - <x_i,x_j>| <= e_i + e_max + e_i e_max
@@ -387,6 +378,21 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
     const double ri = em.err[2 * em.np + i], rmx = em.emax[2];
     eps_g += li * lmx + 1.0001 * (ri + rmx);
   }
+  return eps_g;
+}
+
+template <int RV>
+__global__ void __launch_bounds__(WPB * kWarp)
+k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* __restrict__ part_i, int P,
+          int K, int k1, ErrModel em, double eps_r, const int32_t* __restrict__ rows,
+          const int32_t* __restrict__ count, bool part_by_row, int32_t* fb_rows, int32_t* fb_count,
+          int fb_stat) {
+  __shared__ WarpSmem sm[WPB];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t f = int64_t(blockIdx.x) * WPB + wib;  // position of the row in this launch's row set
+  if (f >= ((rows && count) ? int64_t(*count) : n)) return;
+  const int64_t i = rows ? int64_t(rows[f]) : f;
+  const double eps_g = row_eps_g(em, i);
   WarpSmem& w = sm[wib];
   float B = -FLT_MAX;
   const size_t base = size_t(part_by_row ? i : f) * P * K;
@@ -400,6 +406,194 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
   // row goes to the next, exact stage like an uncertified one.
   const bool ok = cnt >= k1 && refine_warp<RV>(w, cnt, i, k1, B, eps_g, eps_r, io, false, lane);
   if (!ok && lane == 0) {
+    const int slot = atomicAdd(fb_count, 1);
+    fb_rows[slot] = int32_t(i);
+    atomicAdd(reinterpret_cast<unsigned long long*>(io.status + fb_stat), 1ull);
+  }
+}
+
+// Rank of each rescored candidate among [0, n): w.ord[rank] = candidate (one
+// warp).  As in refine_warp: valid positions first, so a malformed list can
+// never send a later read out of range.
+__device__ void rank_cands(WarpSmem& w, int n, int lane) {
+  for (int c = lane; c < n; c += kWarp) w.ord[c] = c;
+  __syncwarp();
+  for (int c = lane; c < n; c += kWarp) {
+    const float sc = w.s[c];
+    const int ic = w.idx[c];
+    int r = 0;
+    for (int e = 0; e < n; ++e) r += ranks_before(w.s[e], w.idx[e], sc, ic) ? 1 : 0;
+    w.ord[r] = c;
+  }
+  __syncwarp();
+}
+
+// Two FP32 dot products of row i (in shared memory) with candidate rows: lane
+// l's FMA chain over float4s l, l + 32, ... and the warp tree, as dot2_fp32
+// and dot4_reg, so the values are identical to theirs.
+__device__ __forceinline__ void dot2_shared(const float4* xi, const float* y0, const float* y1, int dp, int lane,
+                                            float& r0, float& r1) {
+  const float4* b0 = reinterpret_cast<const float4*>(y0);
+  const float4* b1 = reinterpret_cast<const float4*>(y1);
+  float acc0 = 0.f, acc1 = 0.f;
+  for (int q = lane; q < dp / 4; q += kWarp) {
+    const float4 x = xi[q], u = __ldg(b0 + q), v = __ldg(b1 + q);
+    acc0 = fmaf(x.x, u.x, acc0); acc0 = fmaf(x.y, u.y, acc0);
+    acc0 = fmaf(x.z, u.z, acc0); acc0 = fmaf(x.w, u.w, acc0);
+    acc1 = fmaf(x.x, v.x, acc1); acc1 = fmaf(x.y, v.y, acc1);
+    acc1 = fmaf(x.z, v.z, acc1); acc1 = fmaf(x.w, v.w, acc1);
+  }
+  r0 = warp_sum(acc0);
+  r1 = warp_sum(acc1);
+}
+
+// Steps 1-5 for one row with NW warps (the first pass): the row's unit row is
+// staged in shared memory and the warps split every rescoring batch (two
+// candidates per warp at a time), so a row has NW times the loads in flight
+// of the warp-per-row kernel and a thread needs no registers for the row.
+// Warp 0 merges, ranks, certifies and orders; the FP64 near-tie values are
+// split over the warps.  Same arithmetic, same result as k2_refine.
+template <int NW>
+__global__ void __launch_bounds__(NW * kWarp, 48 / NW)
+k2_refine_cta(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* __restrict__ part_i, int P,
+              int Kmax, int k1, ErrModel em, double eps_r, const int32_t* __restrict__ rows,
+              const int32_t* __restrict__ count, bool part_by_row, int32_t* fb_rows, int32_t* fb_count,
+              int fb_stat) {
+  extern __shared__ float4 own[];  // dp / 4 float4: row i
+  __shared__ WarpSmem w;
+  __shared__ float sB;
+  __shared__ int sh[4];            // [0] candidates, [1] next batch end (-1: done), [2] certified, [3] FP64 count
+  const int t = threadIdx.x, wid = t >> 5, lane = t & 31;
+  const int64_t f = blockIdx.x;
+  if (f >= ((rows && count) ? int64_t(*count) : n)) return;
+  const int64_t i = rows ? int64_t(rows[f]) : f;
+  const double eps_g = row_eps_g(em, i);
+  const float4* xi4 = reinterpret_cast<const float4*>(io.xhat + size_t(i) * io.dp);
+  for (int q = t; q < io.dp / 4; q += NW * kWarp) own[q] = __ldg(xi4 + q);
+  if (wid == 0) {
+    float B = -FLT_MAX;
+    const size_t base = size_t(part_by_row ? i : f) * P * Kmax;
+    const bool aborted = (io.status[kStErr] & kErrTimeout) != 0;
+    const int cnt = aborted ? 0 : merge_lists(w, part_s + base, part_i + base, P, Kmax, n, lane, B);
+    if (cnt == n) B = -FLT_MAX;  // every column is a candidate
+    if (lane == 0) {
+      sh[0] = cnt;
+      sB = B;
+    }
+  }
+  __syncthreads();
+  const int Kc = sh[0];
+  bool ok = Kc >= k1;
+  if (ok) {
+    // FP32 scores of candidates [c0, c1) into w.s, two per warp at a time.
+    auto rescore = [&](int c0, int c1) {
+      for (int c = c0 + 2 * wid; c < c1; c += 2 * NW) {
+        const int j0 = w.idx[c];
+        const int j1 = c + 1 < c1 ? w.idx[c + 1] : j0;
+        float v0, v1;
+        dot2_shared(own, io.xhat + size_t(j0) * io.dp, io.xhat + size_t(j1) * io.dp, io.dp, lane, v0, v1);
+        if (lane == 0) {
+          w.s[c] = j0 == i ? 1.0f : v0;
+          if (c + 1 < c1) w.s[c + 1] = j1 == i ? 1.0f : v1;
+        }
+      }
+      __syncthreads();
+    };
+    // Lazy rescoring as in refine_warp: the first k1 + 4, then 8 more at a
+    // time, until the best approximate score left (plus its bound) stays
+    // 3 eps_r below the k1-th rescored score.
+    int K = tmin(Kc, (k1 + 7) & ~3);
+    rescore(0, K);
+    for (;;) {
+      if (wid == 0) {
+        rank_cands(w, K, lane);
+        const bool more = K < Kc && !(double(w.s[w.ord[k1 - 1]]) - 3.0 * eps_r > double(w.g[K]) + eps_g);
+        if (lane == 0) sh[1] = more ? tmin(Kc, K + 8) : -1;
+      }
+      __syncthreads();
+      const int K2 = sh[1];
+      if (K2 < 0) break;
+      rescore(K, K2);
+      K = K2;
+    }
+    // Certificate (every column outside the candidates scores at most B) and
+    // the runs of near-equal FP32 scores that reach into the top-k1.
+    if (wid == 0) {
+      for (int c = lane; c < K; c += kWarp) w.need[c] = 0;
+      __syncwarp();
+      bool cert = true;
+      if (K == Kc && sB > -FLT_MAX) cert = double(w.s[w.ord[k1 - 1]]) - eps_r > double(sB) + eps_g;
+      if (lane == 0) {
+        sh[2] = cert ? 1 : 0;
+        int nneed = 0;
+        if (cert) {
+          int r = 0;
+          while (r < K) {
+            int r1 = r;
+            while (r1 + 1 < K && double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r) ++r1;
+            if (r1 > r && r < k1)
+              for (int q = r; q <= r1; ++q) {
+                w.need[w.ord[q]] = 1;
+                ++nneed;
+              }
+            r = r1 + 1;
+          }
+        }
+        sh[3] = nneed;
+      }
+    }
+    __syncthreads();
+    ok = sh[2] != 0;
+    if (ok) {
+      // FP64 values of the candidates in near-tie runs, one warp each.
+      if (sh[3] > 0) {
+        int seen = 0;
+        for (int c = 0; c < K; ++c) {
+          if (!w.need[c]) continue;
+          if (seen++ % NW != wid) continue;
+          const int j = w.idx[c];
+          double tv = 1.0;
+          if (j != i) tv = dot_fp64_raw(io, i, j, lane) / (io.norm[i] * io.norm[j]);
+          if (lane == 0) w.t[c] = tv;
+        }
+      }
+      __syncthreads();
+      if (wid == 0) {
+        if (lane == 0) {
+          if (sh[3]) atomicAdd(reinterpret_cast<unsigned long long*>(io.status + kStFp64), (unsigned long long)sh[3]);
+          // Re-sort each run by (FP64 value desc, index asc).
+          int r = 0;
+          while (r < K) {
+            if (!w.need[w.ord[r]]) {
+              ++r;
+              continue;
+            }
+            int r1 = r;
+            while (r1 + 1 < K && w.need[w.ord[r1 + 1]] &&
+                   double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r)
+              ++r1;
+            for (int a = r + 1; a <= r1; ++a) {
+              const int c = w.ord[a];
+              int b = a;
+              while (b > r && ranks_before(w.t[c], w.idx[c], w.t[w.ord[b - 1]], w.idx[w.ord[b - 1]])) {
+                w.ord[b] = w.ord[b - 1];
+                --b;
+              }
+              w.ord[b] = c;
+            }
+            r = r1 + 1;
+          }
+        }
+        __syncwarp();
+        for (int r = lane; r < k1; r += kWarp) {
+          const int c = w.ord[r];
+          io.knn_idx[size_t(i) * k1 + r] = w.idx[c];
+          io.knn_score[size_t(i) * k1 + r] = w.need[c] ? float(w.t[c]) : w.s[c];
+        }
+      }
+    }
+  }
+  if (!ok && t == 0) {
     const int slot = atomicAdd(fb_count, 1);
     fb_rows[slot] = int32_t(i);
     atomicAdd(reinterpret_cast<unsigned long long*>(io.status + fb_stat), 1ull);
@@ -487,6 +681,22 @@ static RowIo make_io(const Shape& sh, const void* xq, const void* xg, const floa
 
 double rescore_eps(int dp) { return (dp / 32 + 10) * kU32 * 1.01; }
 
+// Warps per row of the CTA-per-row refinement (0: warp-per-row kernel).  By
+// default 4 for rows of 1,024 floats or more, where the warp-per-row kernel's
+// register-resident row (64 registers) leaves only 16 warps per SM to cover
+// the candidate gathers; RERANK_REFINE_CTA = 0, 4 or 8 forces a choice
+// (identical results).
+static int refine_cta_warps(int dp) {
+  static const int forced = [] {
+    const char* e = std::getenv("RERANK_REFINE_CTA");
+    if (!e) return -1;
+    const int x = std::atoi(e);
+    return (x == 4 || x == 8) ? x : 0;
+  }();
+  if (forced >= 0) return forced;
+  return dp >= 1024 ? 4 : 0;
+}
+
 int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat, const double* norm,
                    const float* part_s, const int32_t* part_i, int P, const ErrModel& em, const int32_t* rows,
                    const int32_t* count, bool part_by_row, int32_t* knn_idx, float* knn_score,
@@ -497,6 +707,18 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
   const unsigned blocks = unsigned((g + WPB - 1) / WPB);
   // First pass: uncertified rows go to the recheck; a recheck's failures go to the exact scan.
   const int stat = fb_stat >= 0 ? fb_stat : ((rows && !part_by_row) ? kStFallback2 : kStFallback);
+  if (refine_cta_warps(sh.dp) > 0) {
+    const size_t smem = size_t(sh.dp) * 4;
+    if (refine_cta_warps(sh.dp) == 8)
+      k2_refine_cta<8><<<unsigned(g), 8 * kWarp, smem, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em,
+                                                             rescore_eps(sh.dp), rows, count, part_by_row, fb_rows,
+                                                             fb_count, stat);
+    else
+      k2_refine_cta<4><<<unsigned(g), 4 * kWarp, smem, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em,
+                                                             rescore_eps(sh.dp), rows, count, part_by_row, fb_rows,
+                                                             fb_count, stat);
+    return 1;
+  }
   // Row i in registers: 4 float4s per lane up to dp = 512, 16 up to 2048.
   if (sh.dp <= 512)
     k2_refine<4><<<blocks, WPB * kWarp, 0, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em, rescore_eps(sh.dp),

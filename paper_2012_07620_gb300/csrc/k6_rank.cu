@@ -497,6 +497,46 @@ size_t rank_smem_fixed(int64_t ng) {
 
 // Test hook: RERANK_TEST_RANK_CAPS="s,b" lowers the bucket sort's limits (s
 // keys in shared memory, buckets of b keys) so that tests reach the global-key
+// Dense final features (h^(0) = x_i): one query per CTA ranks all its gallery
+// scores S[q][0 .. ng), which may be negative.  A score's 32-bit sort key is
+// its IEEE bits mapped to an unsigned order (negatives reversed, -0 taken as
+// +0), inverted so that ascending keys are descending scores; the stable LSD
+// radix sort over the keys in gallery order keeps equal scores in ascending
+// gallery index.  The four key / index arrays live in the CTA's global
+// scratch (4 ng words).
+__global__ void __launch_bounds__(RT, 1)
+k6_rank_dense(const float* __restrict__ S, int64_t nq, int64_t ng, int64_t topk, int32_t* __restrict__ out_idx,
+              float* __restrict__ out_dist, uint32_t* __restrict__ gscratch, const long long* __restrict__ status) {
+  __shared__ uint32_t hist[RW * 256];
+  __shared__ int tmp[32];
+  __shared__ int skip;
+  if (status[kStErr] & kErrOverflow) return;
+  const int t = threadIdx.x;
+  uint32_t* base = gscratch + size_t(blockIdx.x) * size_t(scratch_words(ng));
+  for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    uint32_t* keys = base;
+    uint32_t* vals = base + ng;
+    uint32_t* tkeys = base + 2 * ng;
+    uint32_t* tvals = base + 3 * ng;
+    const float* sq = S + q * ng;
+    for (int64_t g = t; g < ng; g += RT) {
+      const float sc = sq[g];
+      const uint32_t u = sc == 0.0f ? 0u : __float_as_uint(sc);
+      const uint32_t up = (u & 0x80000000u) ? ~u : (u | 0x80000000u);  // ascending with the score
+      keys[g] = ~up;
+      vals[g] = uint32_t(g);
+    }
+    __syncthreads();
+    block_radix_sort(keys, vals, tkeys, tvals, int(ng), hist, tmp, &skip);
+    for (int64_t p = t; p < topk; p += RT) {
+      const uint32_t g = vals[p];
+      out_idx[q * topk + p] = int32_t(g);
+      out_dist[q * topk + p] = 1.0f - sq[g];
+    }
+    __syncthreads();
+  }
+}
+
 // and radix paths on small inputs; all paths give identical lists.
 void rank_caps(int* sort_cap, int* bucket_cap) {
   *sort_cap = SORT_CAP;
@@ -580,5 +620,12 @@ int launch_rank_queries(const Shape& sh, const Buffers& b, int src, int32_t* out
 }
 
 int rank_threads() { return RT; }
+
+int launch_rank_dense(const Shape& sh, const float* S, int32_t* out_idx, float* out_dist, uint32_t* scratch,
+                      long long* status, cudaStream_t s) {
+  const unsigned grid = unsigned(sh.nq < sh.rank_ctas ? sh.nq : sh.rank_ctas);
+  k6_rank_dense<<<grid, RT, 0, s>>>(S, sh.nq, sh.ng, sh.topk, out_idx, out_dist, scratch, status);
+  return 1;
+}
 
 }  // namespace rr

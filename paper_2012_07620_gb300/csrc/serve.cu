@@ -775,6 +775,7 @@ rerank_status serve_load(rerank_ctx* ctx, const void* xg, int64_t ng, int d, int
   const int prec = ctx->cfg.precision;
   if (prec == RERANK_PREC_FP32) return RERANK_EUNSUPPORTED;
   if (ctx->serve) return RERANK_EUNSUPPORTED;
+  if (ctx->cfg.feature_mode == RERANK_FEAT_X) return RERANK_EUNSUPPORTED;  // dense features: rerank_run only
   const int64_t S = sc->max_query;
   const int k1 = sc->k1, k2 = sc->k2, layers = sc->layers;
   rerank_status st = rerank_check_args(S, ng, d, dtype, k1, k2, layers, 0);

@@ -24,7 +24,8 @@ DTYPE = {"f32": 0, "bf16": 1}
 AGGREGATOR = {"sum": 0, "mean": 1, "max": 2}
 FEATURE = {"astar": 0, "a": 1, "x": 2}
 DEBUG = {"knn_idx": 0, "knn_score": 1, "h0_rowptr": 2, "h0_col": 3, "h0_val": 4,
-         "hl_start": 5, "hl_len": 6, "hl_col": 7, "hl_val": 8, "part_s": 9, "part_i": 10, "qerr": 11}
+         "hl_start": 5, "hl_len": 6, "hl_col": 7, "hl_val": 8, "part_s": 9, "part_i": 10, "qerr": 11,
+         "hl_dense": 12}
 
 
 class RerankConfig(ctypes.Structure):
@@ -377,8 +378,8 @@ class Reranker:
         code = DEBUG[what]
         nb = ctypes.c_size_t()
         _check(self._lib.rerank_debug_copy(self._h, code, None, 0, ctypes.byref(nb)), "rerank_debug_copy")
-        dt = {5: np.int64, 1: np.float32, 4: np.float32, 8: np.float32, 9: np.float32, 11: np.float32}.get(code,
-                                                                                                          np.int32)
+        dt = {5: np.int64, 1: np.float32, 4: np.float32, 8: np.float32, 9: np.float32, 11: np.float32,
+              12: np.float32}.get(code, np.int32)
         arr = np.empty(nb.value // np.dtype(dt).itemsize, dtype=dt)
         _check(self._lib.rerank_debug_copy(self._h, code, arr.ctypes.data, arr.nbytes, ctypes.byref(nb)),
                "rerank_debug_copy")

@@ -4,8 +4,10 @@ The paper's default is the sum aggregator over A* rows with alpha = 2
 (Sec. 4.1); it also discusses the mean and max aggregators, the A_i initial
 features (Table 1) and the weight exponent (Eq. 14; alpha = 0 with the mean is
 the query expansion of Sec. 3.4).  Each combination the GPU path implements is
-checked here on a clustered instance with the parity rules of parity.py; the
-dense x_i features are oracle-only and must be refused.
+checked here on a clustered instance with the parity rules of parity.py,
+including the dense x_i initial features (Table 1, first column): with
+L = 0 they give the initial cosine ranking, and with alpha = 0, the mean and
+one layer they are local query expansion (Sec. 3.4, Eq. 4) plus the residual.
 """
 import numpy as np
 import pytest
@@ -65,8 +67,71 @@ def test_max_aggregator_differs_from_sum(lib, inst):
     assert not np.array_equal(outs[0], outs[1])
 
 
-def test_dense_features_are_refused(lib, inst):
+def _dense_run(lib, inst, precision, aggregator, alpha, layers, k1=20, k2=5):
+    with lib.Reranker(precision=precision, aggregator=aggregator, feature="x", alpha=alpha) as R:
+        idx, dist = R.run(torch.from_numpy(inst.xq).cuda(), torch.from_numpy(inst.xg).cuda(), k1, k2, layers)
+        torch.cuda.synchronize()
+        n = len(inst.xq) + len(inst.xg)
+        h = R.debug("hl_dense")
+        knn = R.debug("knn_idx").reshape(n, k1)
+    return idx.cpu().numpy(), dist.cpu().numpy(), h.reshape(n, -1), knn
+
+
+@pytest.mark.parametrize("aggregator,alpha,layers", [
+    ("sum", 2.0, 2),
+    ("mean", 0.0, 1),   # local query expansion + residual (Sec. 3.4)
+    ("max", 2.0, 2),
+    ("sum", 2.0, 0),    # the initial ranking
+    ("mean", 2.0, 3),
+])
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_dense_features_match_oracle(lib, inst, aggregator, alpha, layers, precision):
+    """x_i initial features: h^(L) (dense, Eq. 13-14) and the ranked lists
+    (Alg. 1 step 7) against the oracle's feature="x" run."""
+    k1, k2 = 20, 5
+    ref = o.rerank(inst.xq, inst.xg, k1=k1, k2=k2, layers=layers, alpha=alpha, aggregator=aggregator,
+                   feature="x", mode="dense")
+    idx, dist, h, knn = _dense_run(lib, inst, precision, aggregator, alpha, layers)
+    d = inst.xq.shape[1]
+    np.testing.assert_allclose(h[:, :d], ref.h[-1], rtol=0, atol=2e-6)
+    assert not h[:, d:].any()  # padding columns stay zero
+    assert (knn == ref.knn_idx).all()
+    stats = parity.assert_ranked_equal(idx, dist, ref.s, ref.idx)
+    assert stats["max_dist_err"] < 1e-5
+
+
+def test_dense_features_without_layers_give_the_initial_ranking(lib, inst):
+    """x_i features with L = 0: the list of every query is the gallery sorted by
+    cos(x_q, x_g), ties to the lower index (Table 1, first column = the
+    baseline ranking), checked against SciPy-free FP64 cosines."""
+    idx, dist, _, _ = _dense_run(lib, inst, "fp32", "sum", 2.0, 0)
+    xq = o.unit_rows(inst.xq)
+    xg = o.unit_rows(inst.xg)
+    s = xq @ xg.T
+    want = np.argsort(-s, axis=1, kind="stable")
+    parity.assert_ranked_equal(idx, dist, s, want)
+
+
+def test_dense_one_layer_mean_alpha0_is_query_expansion(lib, inst):
+    """Sec. 3.4: with alpha = 0 and the mean aggregator, one layer gives
+    h_i = normalise(x_i + (1/k2) sum_{j in N(i, k2)} x_j) (Eq. 4 plus the
+    residual of Eq. 13), computed here from the GPU's own neighbour lists."""
+    k1, k2 = 20, 5
+    _, _, h, knn = _dense_run(lib, inst, "fp32", "mean", 0.0, 1, k1, k2)
+    x = o.unit_rows(np.concatenate([inst.xq, inst.xg]))
+    want = x + x[knn[:, :k2]].mean(axis=1)
+    want /= np.linalg.norm(want, axis=1, keepdims=True)
+    np.testing.assert_allclose(h[:, :x.shape[1]], want, rtol=0, atol=2e-6)
+
+
+def test_dense_features_refused_by_batch_and_serving(lib, inst):
+    xq = torch.from_numpy(inst.xq).cuda()
+    xg = torch.from_numpy(inst.xg).cuda()
     with lib.Reranker(feature="x") as R:
         with pytest.raises(lib.RerankError) as e:
-            R.run(torch.from_numpy(inst.xq).cuda(), torch.from_numpy(inst.xg).cuda(), 20, 5, 2)
+            R.run_batch([dict(xq=xq, xg=xg, k1=20, k2=5, layers=2)])
         assert e.value.status == 7  # EUNSUPPORTED
+    with lib.Reranker(precision="bf16", feature="x") as R:
+        with pytest.raises(lib.RerankError) as e:
+            R.load_gallery(xg, max_query=16, k1=20, k2=5, layers=2)
+        assert e.value.status == 7
