@@ -116,7 +116,6 @@ struct TcArgs {
   long long* status;
   const TcInst* insts;      // batched launch: the instances (device memory), else null
   int ninst, items_total;
-  int key_bits;             // packed lists: low key bits holding the column offset in an item
 };
 
 // One work item (a row block against a chunk of column tiles) with the
@@ -224,30 +223,13 @@ __device__ __forceinline__ void drain_delay() {
   for (int k = 0; k < 200; ++k) __nanosleep(1000);
 }
 
-// Packed list entries (BF16 / FP8 main passes).  A score's order-preserving
-// 32-bit key keeps its high 32 - bits bits; the low bits hold the column's
-// offset inside the work item, inverted, so that one unsigned comparison
-// orders entries by (score, then lower column) and a list slot moves with one
-// min and one max.  Scores are thereby grouped into bins of 2^bits keys
-// (relative width 2^(bits - 23)); a list entry's stored score is the upper end
-// of its bin, which bounds the approximate score from above, and a chunk's
-// floor is the lower end of its K-th entry's bin, so every bound the
-// refinement uses still holds.
-__device__ __forceinline__ uint32_t fkey(float f) {
-  const uint32_t u = __float_as_uint(f);
-  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__device__ __forceinline__ float fkey_inv(uint32_t k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
-}
-
 // PAIR: the CTAs of a cluster of two compute 256-row tiles together with
 // tcgen05 cta_group::2.  The even CTA ("leader") issues the MMAs; each CTA
 // loads its own 128 rows of A and its 128 of the tile's 256 B rows, counted
 // on the leader's `full` barrier; the MMA's commits reach both CTAs'
 // `empty` / `tfull` barriers; both CTAs' epilogue warps release an
 // accumulator on the leader's `tempty`.
-template <int MODE, int KL, int EGROUPS, bool BATCH, bool PAIR, bool PACKED>
+template <int MODE, int KL, int EGROUPS, bool BATCH, bool PAIR>
 __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMap* pA1, const CUtensorMap* pB0,
                                         const CUtensorMap* pB1, const CUtensorMap* bmaps, const TcArgs& A) {
   using Smem = SmemOf<PAIR>;
@@ -435,14 +417,8 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
     // and columns li, in registers.  Columns arrive in increasing order, so a
     // new column beats a slot only with a strictly larger score: an equal
     // score keeps the earlier, lower column in front (score desc, column asc).
-    // Packed lists: keys ks (descending) instead of (ls, li).
-    static_assert(!PACKED || !gathered(MODE), "the rechecks keep full-precision lists");
-    constexpr int KLF = PACKED ? 1 : KL;
-    constexpr int KLP = PACKED ? KL : 1;
-    float ls[KLF];
-    int li[KLF];
-    uint32_t ks[KLP];
-    const uint32_t lowmask = PACKED ? (1u << A.key_bits) - 1u : 0u;
+    float ls[KL];
+    int li[KL];
     for (int item = unit; item < items && ok; item += units) {
       TcItem it;
       get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
@@ -451,19 +427,13 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
       const bool live = arow < it.nrows;
       const int64_t grow = gathered(MODE) ? (live ? int64_t(A.rows[arow]) : -1) : it.row0 + arow;  // vertex
 #pragma unroll
-      for (int j = 0; j < KLF; ++j) {
+      for (int j = 0; j < KL; ++j) {
         ls[j] = -FLT_MAX;
         li[j] = kInvalidIdx;
       }
-#pragma unroll
-      for (int j = 0; j < KLP; ++j) ks[j] = 0u;
       // Admission: beat the last slot and reach the floor left by chunks of
       // this row that finished earlier (s >= floor, i.e. s > the float below it).
       const float floor_below = live ? nextafterf(key_score(it.row_floor[arow]), -INFINITY) : INFINITY;
-      // Packed: admit keys whose bin is at least the floor's bin (key > floor bin - 1).
-      const uint32_t floor_bin = live ? (fkey(key_score(it.row_floor[arow])) & ~lowmask) : 0xFFFFFFFFu;
-      const uint32_t kfloor = floor_bin ? floor_bin - 1u : 0u;
-      const int64_t item_col0 = int64_t(it.t0) * TBN;  // B column of the item's first column
       const float rinv = (MODE == MODE_FP8 && live) ? it.inv_scale[grow] : 1.0f;
       for (int ct = it.t0; ct < it.t1; ++ct) {
         const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
@@ -485,52 +455,20 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
           const int nvalid = int(tmin<int64_t>(it.n - lbase, 32));
           const int64_t dself = grow - cbase;
           const int jself = (dself >= 0 && dself < 32) ? int(dself) : -1;
+          const float thr = fmaxf(ls[KL - 1], floor_below);
           uint32_t mask = 0;
-          if constexpr (PACKED) {
-            const uint32_t kthr = umax(ks[KL - 1], kfloor);
-            const uint32_t off0 = uint32_t(lbase - item_col0);
-            uint32_t* kb = reinterpret_cast<uint32_t*>(&sm.batch[eg][0][0]);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              float sc = __uint_as_float(v[j]);
-              if (MODE == MODE_FP8) sc = sc * rinv * __ldg(it.inv_scale + (j < nvalid ? cbase + j : 0));
-              if (j == jself) sc = 1.0f;
-              const uint32_t key = j < nvalid ? (fkey(sc) & ~lowmask) | (lowmask - (off0 + uint32_t(j))) : 0u;
-              kb[j * TBM + r] = key;
-              mask |= (key > kthr) ? (1u << j) : 0u;
-            }
-          } else {
-            const float thr = fmaxf(ls[KLF - 1], floor_below);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              float sc = __uint_as_float(v[j]);
-              if (MODE == MODE_FP8) sc = sc * rinv * __ldg(it.inv_scale + (j < nvalid ? cbase + j : 0));
-              if (j == jself) sc = 1.0f;
-              if (j >= nvalid) sc = -INFINITY;
-              sm.batch[eg][j][r] = sc;
-              mask |= (sc > thr) ? (1u << j) : 0u;
-            }
+          for (int j = 0; j < 32; ++j) {
+            float sc = __uint_as_float(v[j]);
+            if (MODE == MODE_FP8) sc = sc * rinv * __ldg(it.inv_scale + (j < nvalid ? cbase + j : 0));
+            if (j == jself) sc = 1.0f;
+            if (j >= nvalid) sc = -INFINITY;
+            sm.batch[eg][j][r] = sc;
+            mask |= (sc > thr) ? (1u << j) : 0u;
           }
           int rounds = __popc(mask);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(kFull, rounds, o));
-          if constexpr (PACKED) {
-            const uint32_t* kb = reinterpret_cast<const uint32_t*>(&sm.batch[eg][0][0]);
-#pragma unroll 1
-            for (int rd = 0; rd < rounds; ++rd) {
-              uint32_t c = 0u;
-              if (mask) {
-                const int j = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                c = kb[j * TBM + r];
-              }
-              // Keys are distinct: slot j becomes max(min(old j-1, c), old j).
-#pragma unroll
-              for (int j = KL - 1; j > 0; --j) ks[j] = umax(umin(ks[j - 1], c), ks[j]);
-              ks[0] = umax(c, ks[0]);
-            }
-            rounds = 0;
-          }
 #pragma unroll 1
           for (int rd = 0; rd < rounds; ++rd) {
             float cs = -INFINITY;
@@ -546,7 +484,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
             // that is max(min(ls[j-1], cs), ls[j]); the columns follow the same
             // choice.  All tests use the old list: no serial dependency.
 #pragma unroll
-            for (int j = KLF - 1; j > 0; --j) {
+            for (int j = KL - 1; j > 0; --j) {
               const bool bj = cs > ls[j], bp = cs > ls[j - 1];
               li[j] = bp ? li[j - 1] : (bj ? ci : li[j]);
               ls[j] = fmaxf(fminf(ls[j - 1], cs), ls[j]);
@@ -569,26 +507,12 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
         // The K-th best as a running minimum over the first K slots (the list
         // is never indexed dynamically, so it stays in registers).
         float kth = FLT_MAX;
-        if constexpr (PACKED) {
-          const int64_t vcol0 = it.col0 + item_col0;  // vertex of the item's first column
 #pragma unroll
-          for (int j = 0; j < KL; ++j) {
-            if (j < it.K) {
-              const uint32_t key = ks[j];
-              const bool full = key != 0u;
-              it.part_s[o + j] = full ? fkey_inv(key | lowmask) : -FLT_MAX;
-              it.part_i[o + j] = full ? int32_t(vcol0 + int64_t(lowmask - (key & lowmask))) : kInvalidIdx;
-              kth = full ? fminf(kth, fkey_inv(key & ~lowmask)) : -FLT_MAX;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < KLF; ++j) {
-            if (j < it.K) {
-              it.part_s[o + j] = ls[j];
-              it.part_i[o + j] = li[j];
-              kth = fminf(kth, ls[j]);
-            }
+        for (int j = 0; j < KL; ++j) {
+          if (j < it.K) {
+            it.part_s[o + j] = ls[j];
+            it.part_i[o + j] = li[j];
+            kth = fminf(kth, ls[j]);
           }
         }
         // This chunk's K-th best becomes a floor for the row's later chunks.
@@ -618,27 +542,27 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
   }
 }
 
-template <int MODE, int KL, int EGROUPS, bool PACKED>
+template <int MODE, int KL, int EGROUPS>
 __global__ void __launch_bounds__(threads_of(EGROUPS), 1)
 k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
            const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs A) {
-  tc_body<MODE, KL, EGROUPS, false, false, PACKED>(&mA0, &mA1, &mB0, &mB1, nullptr, A);
+  tc_body<MODE, KL, EGROUPS, false, false>(&mA0, &mA1, &mB0, &mB1, nullptr, A);
 }
 
 // CTA pairs (launched in clusters of two): 256-row items, one cta_group::2
 // MMA per k-step for both SMs.
-template <int MODE, int KL, int EGROUPS, bool PACKED>
+template <int MODE, int KL, int EGROUPS>
 __global__ void __launch_bounds__(threads_of(EGROUPS), 1)
 k1_tc2_topk(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, TcArgs A) {
-  tc_body<MODE, KL, EGROUPS, false, true, PACKED>(&mA, &mA, &mB, &mB, nullptr, A);
+  tc_body<MODE, KL, EGROUPS, false, true>(&mA, &mA, &mB, &mB, nullptr, A);
 }
 
 // Many instances in one persistent launch: the items of all instances form one
 // list that the CTAs walk; each item carries its instance's parameters.
-template <int MODE, int KL, int EGROUPS, bool PACKED>
+template <int MODE, int KL, int EGROUPS>
 __global__ void __launch_bounds__(threads_of(EGROUPS), 1)
 k1_tc_topk_batch(const __grid_constant__ TcMaps maps, TcArgs A) {
-  tc_body<MODE, KL, EGROUPS, true, false, PACKED>(nullptr, nullptr, nullptr, nullptr, maps.m, A);
+  tc_body<MODE, KL, EGROUPS, true, false>(nullptr, nullptr, nullptr, nullptr, maps.m, A);
 }
 
 // Test hook: RERANK_TEST_TC_STALL set in the environment makes the kernels'
@@ -679,25 +603,18 @@ template <int MODE, int KL, int EG>
 void launch_kl(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
                const TcArgs& A, int grid, cudaStream_t s) {
   const size_t smem = sizeof(TcSmem) + 1024;
-  if constexpr (!gathered(MODE)) {
-    if (A.key_bits > 0) {
-      cudaFuncSetAttribute(k1_tc_topk<MODE, KL, EG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      k1_tc_topk<MODE, KL, EG, true><<<grid, threads_of(EG), smem, s>>>(a0, a1, b0, b1, A);
-      return;
-    }
-  }
-  cudaFuncSetAttribute(k1_tc_topk<MODE, KL, EG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  k1_tc_topk<MODE, KL, EG, false><<<grid, threads_of(EG), smem, s>>>(a0, a1, b0, b1, A);
+  cudaFuncSetAttribute(k1_tc_topk<MODE, KL, EG>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  k1_tc_topk<MODE, KL, EG><<<grid, threads_of(EG), smem, s>>>(a0, a1, b0, b1, A);
 }
 
 // Pairs that can be resident at once (clusters of two, one CTA per SM); 0 if
 // the query fails.
-template <int MODE, int KL, int EG, bool PK>
+template <int MODE, int KL, int EG>
 int pair_units(int sm_count) {
   static int cached = -1;
   if (cached < 0) {
     const size_t smem = sizeof(TcSmemPair) + 1024;
-    cudaFuncSetAttribute(k1_tc2_topk<MODE, KL, EG, PK>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k1_tc2_topk<MODE, KL, EG>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(unsigned(sm_count & ~1));
     cfg.blockDim = dim3(threads_of(EG));
@@ -710,7 +627,7 @@ int pair_units(int sm_count) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, k1_tc2_topk<MODE, KL, EG, PK>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&n, k1_tc2_topk<MODE, KL, EG>, &cfg) != cudaSuccess) {
       cudaGetLastError();
       n = 0;
     }
@@ -719,10 +636,10 @@ int pair_units(int sm_count) {
   return cached;
 }
 
-template <int MODE, int KL, int EG, bool PK>
+template <int MODE, int KL, int EG>
 bool launch_kl_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A, int items, int sm_count,
                     cudaStream_t s) {
-  const int units = pair_units<MODE, KL, EG, PK>(sm_count);
+  const int units = pair_units<MODE, KL, EG>(sm_count);
   if (units < 1) return false;
   const size_t smem = sizeof(TcSmemPair) + 1024;
   cudaLaunchConfig_t cfg{};
@@ -737,32 +654,17 @@ bool launch_kl_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A,
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k1_tc2_topk<MODE, KL, EG, PK>, a, b, A) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, k1_tc2_topk<MODE, KL, EG>, a, b, A) == cudaSuccess;
 }
 
-template <int MODE, bool PK>
-bool launch_mode_pair_pk(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A, int eg, int items,
-                         int sm_count, cudaStream_t s) {
-  if (A.K <= 48)
-    return eg == 2 ? launch_kl_pair<MODE, 48, 2, PK>(a, b, A, items, sm_count, s)
-                   : launch_kl_pair<MODE, 48, 1, PK>(a, b, A, items, sm_count, s);
-  return eg == 2 ? launch_kl_pair<MODE, KLIST, 2, PK>(a, b, A, items, sm_count, s)
-                 : launch_kl_pair<MODE, KLIST, 1, PK>(a, b, A, items, sm_count, s);
-}
 template <int MODE>
 bool launch_mode_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A, int eg, int items, int sm_count,
                       cudaStream_t s) {
-  return A.key_bits > 0 ? launch_mode_pair_pk<MODE, true>(a, b, A, eg, items, sm_count, s)
-                        : launch_mode_pair_pk<MODE, false>(a, b, A, eg, items, sm_count, s);
-}
-
-// Low key bits for items of up to `cols` columns; 0 (full-precision lists)
-// when an item is wider than 2^14 columns, so that a bin is never wider than
-// 2^-9 of the score.
-int key_bits_for(int64_t cols) {
-  int bits = 8;
-  while (bits <= 14 && (int64_t(1) << bits) < cols) ++bits;
-  return bits <= 14 ? bits : 0;
+  if (A.K <= 48)
+    return eg == 2 ? launch_kl_pair<MODE, 48, 2>(a, b, A, items, sm_count, s)
+                   : launch_kl_pair<MODE, 48, 1>(a, b, A, items, sm_count, s);
+  return eg == 2 ? launch_kl_pair<MODE, KLIST, 2>(a, b, A, items, sm_count, s)
+                 : launch_kl_pair<MODE, KLIST, 1>(a, b, A, items, sm_count, s);
 }
 
 // The per-row list lives in registers, so its length is a compile-time choice.
@@ -809,15 +711,6 @@ bool tc_pairs() {
   return on != 0;
 }
 int tc_item_rows() { return tc_pairs() ? 2 * TBM : TBM; }
-// Whether the main passes keep packed (score bin, column) keys; RERANK_TC_PACKED=0
-// selects full-precision lists (the refined lists are the same either way).
-bool tc_packed() {
-  static const int on = [] {
-    const char* e = std::getenv("RERANK_TC_PACKED");
-    return (e && e[0] == '0') ? 0 : 1;
-  }();
-  return on != 0;
-}
 int tc_lists_per_chunk(int dp, int segs) { return dp * segs <= 1024 ? 2 : 1; }
 static_assert(sizeof(TcSmem) + 1024 <= 227 * 1024, "shared memory of the tensor-core kernel");
 int tc_kmax() { return KLIST; }
@@ -848,7 +741,6 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   A.part_i = part_i;
   A.status = status;
   A.stall = stall_hook();
-  A.key_bits = tc_packed() ? key_bits_for(int64_t((A.col_tiles + A.chunks - 1) / A.chunks) * TBN) : 0;
   const int items = A.row_blocks * A.chunks;
   if (pairs) {
     const bool ok = fp8 ? launch_mode_pair<MODE_FP8>(map, map, A, eg, items, sm_count, s)
@@ -891,7 +783,6 @@ int launch_sim_tc_rect_topk(const Shape& sh, const void* a, int64_t a_rows, int6
   A.part_i = part_i;
   A.status = status;
   A.stall = stall_hook();
-  A.key_bits = tc_packed() ? key_bits_for(int64_t((A.col_tiles + A.chunks - 1) / A.chunks) * TBN) : 0;
   const int items = A.row_blocks * A.chunks;
   const int grid = items < sm_count ? items : sm_count;
   if (fp8)
@@ -941,7 +832,6 @@ int launch_sim_tc_batch(const TcBatchInst* in, int ninst, bool fp8, void* insts_
   TcMaps maps;
   TcInst* hi = static_cast<TcInst*>(staging);
   int items = 0, kmax = 0;
-  int64_t max_item_cols = 0;
   for (int k = 0; k < ninst; ++k) {
     const TcBatchInst& b = in[k];
     if (tc_lists_per_chunk(b.dp, 1) != eg) return -1;
@@ -962,8 +852,6 @@ int launch_sim_tc_batch(const TcBatchInst* in, int ninst, bool fp8, void* insts_
     t.status = b.status;
     items += t.row_blocks * t.chunks;
     kmax = b.K > kmax ? b.K : kmax;
-    const int64_t cols = int64_t((t.col_tiles + t.chunks - 1) / t.chunks) * TBN;
-    max_item_cols = cols > max_item_cols ? cols : max_item_cols;
     cudaMemsetAsync(b.row_floor, kFloorResetByte, sizeof(int) * size_t(b.n), s);
   }
   cudaMemcpyAsync(insts_dev, staging, sizeof(TcInst) * size_t(ninst), cudaMemcpyHostToDevice, s);
@@ -980,25 +868,12 @@ int launch_sim_tc_batch(const TcBatchInst* in, int ninst, bool fp8, void* insts_
     kernel<<<grid, threads_of(eg), smem, s>>>(maps, A);
   };
   const bool k48 = kmax <= 48;
-  A.key_bits = tc_packed() ? key_bits_for(max_item_cols) : 0;
-  // Packed lists whenever the widest item allows them (key_bits > 0).
-  if (A.key_bits > 0) {
-    if (fp8) {
-      if (eg == 2) k48 ? go(k1_tc_topk_batch<MODE_FP8, 48, 2, true>) : go(k1_tc_topk_batch<MODE_FP8, KLIST, 2, true>);
-      else k48 ? go(k1_tc_topk_batch<MODE_FP8, 48, 1, true>) : go(k1_tc_topk_batch<MODE_FP8, KLIST, 1, true>);
-    } else {
-      if (eg == 2) k48 ? go(k1_tc_topk_batch<MODE_BF16, 48, 2, true>) : go(k1_tc_topk_batch<MODE_BF16, KLIST, 2, true>);
-      else k48 ? go(k1_tc_topk_batch<MODE_BF16, 48, 1, true>) : go(k1_tc_topk_batch<MODE_BF16, KLIST, 1, true>);
-    }
+  if (fp8) {
+    if (eg == 2) k48 ? go(k1_tc_topk_batch<MODE_FP8, 48, 2>) : go(k1_tc_topk_batch<MODE_FP8, KLIST, 2>);
+    else k48 ? go(k1_tc_topk_batch<MODE_FP8, 48, 1>) : go(k1_tc_topk_batch<MODE_FP8, KLIST, 1>);
   } else {
-    if (fp8) {
-      if (eg == 2) k48 ? go(k1_tc_topk_batch<MODE_FP8, 48, 2, false>) : go(k1_tc_topk_batch<MODE_FP8, KLIST, 2, false>);
-      else k48 ? go(k1_tc_topk_batch<MODE_FP8, 48, 1, false>) : go(k1_tc_topk_batch<MODE_FP8, KLIST, 1, false>);
-    } else {
-      if (eg == 2) k48 ? go(k1_tc_topk_batch<MODE_BF16, 48, 2, false>)
-                   : go(k1_tc_topk_batch<MODE_BF16, KLIST, 2, false>);
-      else k48 ? go(k1_tc_topk_batch<MODE_BF16, 48, 1, false>) : go(k1_tc_topk_batch<MODE_BF16, KLIST, 1, false>);
-    }
+    if (eg == 2) k48 ? go(k1_tc_topk_batch<MODE_BF16, 48, 2>) : go(k1_tc_topk_batch<MODE_BF16, KLIST, 2>);
+    else k48 ? go(k1_tc_topk_batch<MODE_BF16, 48, 1>) : go(k1_tc_topk_batch<MODE_BF16, KLIST, 1>);
   }
   return 1;
 }
