@@ -247,12 +247,10 @@ def _config(args, w):
 
 
 # DRAM bytes (read + write) of one similarity launch, from `ncu --set full` captures
-# (profiles/k1_tc_topk_bf16_market_23k_d2048.md); None where no capture of the
-# current kernel exists.
-SIM_TRAFFIC_BYTES = {("bf16", "market"): 389.4e6}
-# DRAM bytes of the refinement's first pass, same source
-# (profiles/k2_refine_bf16_market_23k_d2048.md).
-REFINE_DRAM_BYTES = {("bf16", "market"): 1.599e9}
+# of the current kernel (profiles/); None where no capture of it exists.
+SIM_TRAFFIC_BYTES = {}
+# DRAM bytes of the refinement's first pass, same source.
+REFINE_DRAM_BYTES = {}
 
 
 def _stage_rooflines(precision, stages, nq, ng, d, k1, k2, rescore_m, h_nnz, layers, workload):

@@ -110,16 +110,14 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
     }
     b.ahi = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
     b.alo = c.take<__nv_bfloat16>(size_t(np) * sh.dp);
-    const size_t p3 = size_t(std::max(sh.P3, sh.P3g));
-    b.part3_s = c.take<float>(size_t(n) * p3 * sh.K);
-    b.part3_i = c.take<int32_t>(size_t(n) * p3 * sh.K);
+    const size_t p3k = std::max(size_t(sh.P3) * sh.K, size_t(sh.P3g) * sh.K3);
+    b.part3_s = c.take<float>(size_t(n) * p3k);
+    b.part3_i = c.take<int32_t>(size_t(n) * p3k);
     b.row_floor3 = c.take<int>(size_t(n));
     b.fb2_rows = c.take<int32_t>(size_t(n));
     b.fb2_count = c.take<int32_t>(4);
-    if (precision == RERANK_PREC_FP8) {
-      b.fb3_rows = c.take<int32_t>(size_t(n));
-      b.fb3_count = c.take<int32_t>(4);
-    }
+    b.fb3_rows = c.take<int32_t>(size_t(n));
+    b.fb3_count = c.take<int32_t>(4);
   }
   b.row_floor = c.take<int>(size_t(n));
   b.nb4 = c.take<int32_t>(4 * size_t(n));
@@ -321,18 +319,24 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
     const int32_t* split_rows = b.fb_rows;
     const int32_t* split_count = b.fb_count;
     if (prec == RERANK_PREC_FP8) {
-      // FP8 leaves most rows uncertified (its bound is ~0.07): a BF16 stage
-      // (the hi copies, one product, bound ~2e-3) first, the hi/lo split only
-      // for what that cannot certify.
-      const int rg = launch_sim_tc_gather_topk(sh, sh.P3g, b.ahi, b.xhi, b.fb_rows, b.fb_count, b.row_floor3,
+      // FP8 leaves most rows uncertified (its bound is ~0.07): a single-product
+      // BF16 stage (the hi copies, bound ~3e-3) with the longest candidate
+      // lists (K3 = 64) first, the hi/lo split only for what that cannot
+      // certify.  (For BF16 rows the same stage certifies nearly every row
+      // but costs as much as the split: its loose bound makes the rescoring
+      // go ~50 candidates deep instead of ~27.)
+      Shape sh3 = sh;
+      sh3.K = sh.K3;
+      const int rg = launch_sim_tc_gather_topk(sh3, sh.P3g, b.ahi, b.xhi, b.fb_rows, b.fb_count, b.row_floor3,
                                                b.part3_s, b.part3_i, status, ctx->sm_count, s);
       if (rg < 0) return RERANK_ECUDA;
       nl += rg;
+      // the hi copy is not the FP8 copy: its own bound ||x - hi|| = ||lo + r||
       ErrModel eh = em;
       eh.kind = 3;
       eh.eps = (sh.dp / 16 + 32) * 2.0 * kU32 + 8.0 * kU32;
-      nl += launch_refine(sh, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3g, eh, b.fb_rows, b.fb_count, false,
-                          b.knn_idx, b.knn_score, b.fb3_rows, b.fb3_count, status, s, -1, kStFallbackMid);
+      nl += launch_refine(sh3, dq, dg, b.xhat, b.norm, b.part3_s, b.part3_i, sh.P3g, eh, b.fb_rows, b.fb_count,
+                          false, b.knn_idx, b.knn_score, b.fb3_rows, b.fb3_count, status, s, -1, kStFallbackMid);
       nl += launch_gather_rows(b.fb3_rows, b.fb3_count, b.xhi, b.xlo, b.ahi, b.alo, sh.n, sh.dp, s);
       split_rows = b.fb3_rows;
       split_count = b.fb3_count;
@@ -545,6 +549,7 @@ rerank_status plan_shape(const rerank_ctx* ctx, int64_t nq, int64_t ng, int d, i
   // The recheck covers an unknown, usually small, set of rows: many short chunks keep every SM busy.
   sh.P3 = tc ? int(std::min<int64_t>(32 / lpc3, sh.np / 256)) * lpc3 : 0;
   sh.P3g = prec == RERANK_PREC_FP8 ? int(std::min<int64_t>(32 / lpc, sh.np / 256)) * lpc : 0;
+  sh.K3 = prec == RERANK_PREC_FP8 ? int(std::max<int64_t>(sh.K, std::min<int64_t>(kmax, sh.n))) : 0;
   // Capacity of a propagation layer: sum over rows of ub_i <= min(n, sum_j len_j).
   // n^2 bounds it exactly for small graphs; otherwise a generous guess, grown on overflow.
   int64_t guess = std::max<int64_t>(2 * sh.n * k1, std::min<int64_t>(sh.n * sh.n, sh.n * int64_t(k2 + 1) * 160));
@@ -650,7 +655,7 @@ uint64_t buffer_id(const void* p) {
 // workspace offset they fix everything a batched call enqueues for it.
 void shape_key(const Shape& sh, std::vector<int64_t>& k) {
   const int64_t v[] = {sh.nq, sh.ng, sh.n, sh.np, sh.d, sh.dp, sh.dtype, sh.k1, sh.k2, sh.layers, sh.K, sh.P, sh.P3,
-                       sh.P3g, sh.topk, sh.host_in, sh.host_out, sh.knn_only, sh.ext_feat, sh.cap_h, sh.cap_csc,
+                       sh.P3g, sh.K3, sh.topk, sh.host_in, sh.host_out, sh.knn_only, sh.ext_feat, sh.cap_h, sh.cap_csc,
                        sh.hash_slots, sh.rank_ctas, sh.rank_scratch_per_cta, sh.tune.sim_chunks, sh.tune.prop_warps,
                        sh.tune.refine_order, sh.tune.rescore_m, sh.tune.rank_threads};
   k.insert(k.end(), std::begin(v), std::end(v));

@@ -30,7 +30,7 @@ enum : int {
   kStFallback2 = 5,    // rows that needed the exact full-row scan
   kStNeed = 4,         // capacity needed by the stage that overflowed (elements)
   kStTouched = 6,      // serving: gallery rows whose neighbour list a request re-derived
-  kStFallbackMid = 7,  // FP8 path: rows the BF16 recheck stage could not certify
+  kStFallbackMid = 7,  // FP8 path: rows the single-product BF16 recheck stage could not certify
   kStNnz0 = 8,         // nnz of h^(l) at kStNnz0 + l, l <= 8
   kStRecomputed = 17,  // serving: layer rows recomputed (not taken from the gallery's own graph)
   kStCount = 32

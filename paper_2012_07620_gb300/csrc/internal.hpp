@@ -73,7 +73,7 @@ struct Buffers {
   int* row_floor3 = nullptr;     // n
   int32_t* fb2_rows = nullptr;   // n: rows left for the exact scan
   int32_t* fb2_count = nullptr;
-  int32_t* fb3_rows = nullptr;   // n: FP8 path, rows left after the BF16 stage
+  int32_t* fb3_rows = nullptr;   // n: FP8 path, rows left after the single-product BF16 recheck stage
   int32_t* fb3_count = nullptr;
   int* row_floor = nullptr;      // n, shared K-th best per row (similarity kernels)
   int32_t* nb4 = nullptr;        // 4n: best candidates per row (processing order)
@@ -132,7 +132,8 @@ struct Shape {
   int d = 0, dp = 0, dtype = 0;
   int k1 = 0, k2 = 0, layers = 0, K = 0, P = 0;
   int P3 = 0;              // candidate lists per row of the hi/lo recheck
-  int P3g = 0;             // FP8 path: lists per row of the BF16 recheck stage
+  int P3g = 0;             // FP8 path: lists per row of the single-product BF16 recheck stage
+  int K3 = 0;              // FP8 path: candidates per list of that stage (the longest list the kernels hold)
   int64_t topk = 0;
   bool host_in = false, host_out = false;
   bool knn_only = false;

@@ -431,17 +431,28 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
         ls[j] = -FLT_MAX;
         li[j] = kInvalidIdx;
       }
-      // Admission: beat the last slot and reach the floor left by chunks of
-      // this row that finished earlier (s >= floor, i.e. s > the float below it).
-      const float floor_below = live ? nextafterf(key_score(it.row_floor[arow]), -INFINITY) : INFINITY;
+      // Admission: beat the last slot and reach the row's floor (s >= floor,
+      // i.e. s > the float below it).  The floor is the best K-th score any
+      // chunk of this row has published: chunks publish their running K-th
+      // after every tile, and an item re-reads the floor before every tile,
+      // so chunks of a row that run at the same time raise each other's bar.
+      // A partial list's K-th best is at most the row's final K-th best, so a
+      // column below the floor can never be among the row's K best.
+      int seen = live ? __ldcg(it.row_floor + arow) : INT_MAX;  // floor key in use (also: last published)
+      float floor_below = live ? nextafterf(key_score(seen), -INFINITY) : INFINITY;
       const float rinv = (MODE == MODE_FP8 && live) ? it.inv_scale[grow] : 1.0f;
       for (int ct = it.t0; ct < it.t1; ++ct) {
+        const int fk = (live && ct > it.t0) ? __ldcg(it.row_floor + arow) : seen;
         const uint32_t ab = tcount & 1u, tph = (tcount >> 1) & 1u;
         if (!tc::mbar_wait(&sm.tfull[ab], tph, abort, WAIT_LIMIT)) {
           ok = false;
           break;
         }
         tc::tc_fence_after();
+        if (fk > seen) {
+          seen = fk;
+          floor_below = nextafterf(key_score(fk), -INFINITY);
+        }
 #pragma unroll 1
         for (int cb = eg * (TBN / 32 / EGROUPS); cb < (eg + 1) * (TBN / 32 / EGROUPS); ++cb) {
           uint32_t v[32];
@@ -500,6 +511,21 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
           else tc::mbar_arrive(&sm.tempty[ab]);
         }
         ++tcount;
+        // Publish this chunk's running K-th best when it raises the row's floor.
+        if (live && ct + 1 < it.t1) {
+          float kth = FLT_MAX;
+#pragma unroll
+          for (int j = 0; j < KL; ++j)
+            if (j < it.K) kth = fminf(kth, ls[j]);
+          if (kth != -FLT_MAX) {
+            const int key = score_key(kth);
+            if (key > seen) {
+              atomicMax(it.row_floor + arow, key);
+              seen = key;
+              floor_below = nextafterf(kth, -INFINITY);
+            }
+          }
+        }
       }
       if (!ok) break;
       if (live) {

@@ -389,26 +389,30 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
           int fb_stat) {
   __shared__ WarpSmem sm[WPB];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t f = int64_t(blockIdx.x) * WPB + wib;  // position of the row in this launch's row set
-  if (f >= ((rows && count) ? int64_t(*count) : n)) return;
-  const int64_t i = rows ? int64_t(rows[f]) : f;
-  const double eps_g = row_eps_g(em, i);
-  WarpSmem& w = sm[wib];
-  float B = -FLT_MAX;
-  const size_t base = size_t(part_by_row ? i : f) * P * K;
-  // After a similarity stage that timed out, its lists may be unwritten (any
-  // bits, repeated columns): they are not read, and every row goes on to the
-  // exact stage as one with no candidates.
-  const bool aborted = (io.status[kStErr] & kErrTimeout) != 0;
-  const int cnt = aborted ? 0 : merge_lists(w, part_s + base, part_i + base, P, K, n, lane, B);
-  if (cnt == n) B = -FLT_MAX;  // every column is a candidate
-  // Fewer than k1 candidates (only after an aborted similarity stage): the
-  // row goes to the next, exact stage like an uncertified one.
-  const bool ok = cnt >= k1 && refine_warp<RV>(w, cnt, i, k1, B, eps_g, eps_r, io, false, lane);
-  if (!ok && lane == 0) {
-    const int slot = atomicAdd(fb_count, 1);
-    fb_rows[slot] = int32_t(i);
-    atomicAdd(reinterpret_cast<unsigned long long*>(io.status + fb_stat), 1ull);
+  const int64_t limit = (rows && count) ? int64_t(*count) : n;
+  // f: position of the row in this launch's row set (grid-stride: a gathered
+  // row set's size is known on the device only)
+  for (int64_t f = int64_t(blockIdx.x) * WPB + wib; f < limit; f += int64_t(gridDim.x) * WPB) {
+    const int64_t i = rows ? int64_t(rows[f]) : f;
+    const double eps_g = row_eps_g(em, i);
+    WarpSmem& w = sm[wib];
+    float B = -FLT_MAX;
+    const size_t base = size_t(part_by_row ? i : f) * P * K;
+    // After a similarity stage that timed out, its lists may be unwritten (any
+    // bits, repeated columns): they are not read, and every row goes on to the
+    // exact stage as one with no candidates.
+    const bool aborted = (io.status[kStErr] & kErrTimeout) != 0;
+    const int cnt = aborted ? 0 : merge_lists(w, part_s + base, part_i + base, P, K, n, lane, B);
+    if (cnt == n) B = -FLT_MAX;  // every column is a candidate
+    // Fewer than k1 candidates (only after an aborted similarity stage): the
+    // row goes to the next, exact stage like an uncertified one.
+    const bool ok = cnt >= k1 && refine_warp<RV>(w, cnt, i, k1, B, eps_g, eps_r, io, false, lane);
+    if (!ok && lane == 0) {
+      const int slot = atomicAdd(fb_count, 1);
+      fb_rows[slot] = int32_t(i);
+      atomicAdd(reinterpret_cast<unsigned long long*>(io.status + fb_stat), 1ull);
+    }
+    __syncwarp();
   }
 }
 
@@ -464,139 +468,141 @@ k2_refine_cta(RowIo io, int64_t n, const float* __restrict__ part_s, const int32
   __shared__ float sB;
   __shared__ int sh[4];            // [0] candidates, [1] next batch end (-1: done), [2] certified, [3] FP64 count
   const int t = threadIdx.x, wid = t >> 5, lane = t & 31;
-  const int64_t f = blockIdx.x;
-  if (f >= ((rows && count) ? int64_t(*count) : n)) return;
-  const int64_t i = rows ? int64_t(rows[f]) : f;
-  const double eps_g = row_eps_g(em, i);
-  const float4* xi4 = reinterpret_cast<const float4*>(io.xhat + size_t(i) * io.dp);
-  for (int q = t; q < io.dp / 4; q += NW * kWarp) own[q] = __ldg(xi4 + q);
-  if (wid == 0) {
-    float B = -FLT_MAX;
-    const size_t base = size_t(part_by_row ? i : f) * P * Kmax;
-    const bool aborted = (io.status[kStErr] & kErrTimeout) != 0;
-    const int cnt = aborted ? 0 : merge_lists(w, part_s + base, part_i + base, P, Kmax, n, lane, B);
-    if (cnt == n) B = -FLT_MAX;  // every column is a candidate
-    if (lane == 0) {
-      sh[0] = cnt;
-      sB = B;
-    }
-  }
-  __syncthreads();
-  const int Kc = sh[0];
-  bool ok = Kc >= k1;
-  if (ok) {
-    // FP32 scores of candidates [c0, c1) into w.s, two per warp at a time.
-    auto rescore = [&](int c0, int c1) {
-      for (int c = c0 + 2 * wid; c < c1; c += 2 * NW) {
-        const int j0 = w.idx[c];
-        const int j1 = c + 1 < c1 ? w.idx[c + 1] : j0;
-        float v0, v1;
-        dot2_shared(own, io.xhat + size_t(j0) * io.dp, io.xhat + size_t(j1) * io.dp, io.dp, lane, v0, v1);
-        if (lane == 0) {
-          w.s[c] = j0 == i ? 1.0f : v0;
-          if (c + 1 < c1) w.s[c + 1] = j1 == i ? 1.0f : v1;
-        }
-      }
-      __syncthreads();
-    };
-    // Lazy rescoring as in refine_warp: the first k1 + 4, then 8 more at a
-    // time, until the best approximate score left (plus its bound) stays
-    // 3 eps_r below the k1-th rescored score.
-    int K = tmin(Kc, (k1 + 7) & ~3);
-    rescore(0, K);
-    for (;;) {
-      if (wid == 0) {
-        rank_cands(w, K, lane);
-        const bool more = K < Kc && !(double(w.s[w.ord[k1 - 1]]) - 3.0 * eps_r > double(w.g[K]) + eps_g);
-        if (lane == 0) sh[1] = more ? tmin(Kc, K + 8) : -1;
-      }
-      __syncthreads();
-      const int K2 = sh[1];
-      if (K2 < 0) break;
-      rescore(K, K2);
-      K = K2;
-    }
-    // Certificate (every column outside the candidates scores at most B) and
-    // the runs of near-equal FP32 scores that reach into the top-k1.
+  const int64_t limit = (rows && count) ? int64_t(*count) : n;
+  for (int64_t f = blockIdx.x; f < limit; f += gridDim.x) {  // grid-stride, as in k2_refine
+    const int64_t i = rows ? int64_t(rows[f]) : f;
+    const double eps_g = row_eps_g(em, i);
+    const float4* xi4 = reinterpret_cast<const float4*>(io.xhat + size_t(i) * io.dp);
+    for (int q = t; q < io.dp / 4; q += NW * kWarp) own[q] = __ldg(xi4 + q);
     if (wid == 0) {
-      for (int c = lane; c < K; c += kWarp) w.need[c] = 0;
-      __syncwarp();
-      bool cert = true;
-      if (K == Kc && sB > -FLT_MAX) cert = double(w.s[w.ord[k1 - 1]]) - eps_r > double(sB) + eps_g;
+      float B = -FLT_MAX;
+      const size_t base = size_t(part_by_row ? i : f) * P * Kmax;
+      const bool aborted = (io.status[kStErr] & kErrTimeout) != 0;
+      const int cnt = aborted ? 0 : merge_lists(w, part_s + base, part_i + base, P, Kmax, n, lane, B);
+      if (cnt == n) B = -FLT_MAX;  // every column is a candidate
       if (lane == 0) {
-        sh[2] = cert ? 1 : 0;
-        int nneed = 0;
-        if (cert) {
-          int r = 0;
-          while (r < K) {
-            int r1 = r;
-            while (r1 + 1 < K && double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r) ++r1;
-            if (r1 > r && r < k1)
-              for (int q = r; q <= r1; ++q) {
-                w.need[w.ord[q]] = 1;
-                ++nneed;
-              }
-            r = r1 + 1;
-          }
-        }
-        sh[3] = nneed;
+        sh[0] = cnt;
+        sB = B;
       }
     }
     __syncthreads();
-    ok = sh[2] != 0;
+    const int Kc = sh[0];
+    bool ok = Kc >= k1;
     if (ok) {
-      // FP64 values of the candidates in near-tie runs, one warp each.
-      if (sh[3] > 0) {
-        int seen = 0;
-        for (int c = 0; c < K; ++c) {
-          if (!w.need[c]) continue;
-          if (seen++ % NW != wid) continue;
-          const int j = w.idx[c];
-          double tv = 1.0;
-          if (j != i) tv = dot_fp64_raw(io, i, j, lane) / (io.norm[i] * io.norm[j]);
-          if (lane == 0) w.t[c] = tv;
+      // FP32 scores of candidates [c0, c1) into w.s, two per warp at a time.
+      auto rescore = [&](int c0, int c1) {
+        for (int c = c0 + 2 * wid; c < c1; c += 2 * NW) {
+          const int j0 = w.idx[c];
+          const int j1 = c + 1 < c1 ? w.idx[c + 1] : j0;
+          float v0, v1;
+          dot2_shared(own, io.xhat + size_t(j0) * io.dp, io.xhat + size_t(j1) * io.dp, io.dp, lane, v0, v1);
+          if (lane == 0) {
+            w.s[c] = j0 == i ? 1.0f : v0;
+            if (c + 1 < c1) w.s[c + 1] = j1 == i ? 1.0f : v1;
+          }
+        }
+        __syncthreads();
+      };
+      // Lazy rescoring as in refine_warp: the first k1 + 4, then 8 more at a
+      // time, until the best approximate score left (plus its bound) stays
+      // 3 eps_r below the k1-th rescored score.
+      int K = tmin(Kc, (k1 + 7) & ~3);
+      rescore(0, K);
+      for (;;) {
+        if (wid == 0) {
+          rank_cands(w, K, lane);
+          const bool more = K < Kc && !(double(w.s[w.ord[k1 - 1]]) - 3.0 * eps_r > double(w.g[K]) + eps_g);
+          if (lane == 0) sh[1] = more ? tmin(Kc, K + 8) : -1;
+        }
+        __syncthreads();
+        const int K2 = sh[1];
+        if (K2 < 0) break;
+        rescore(K, K2);
+        K = K2;
+      }
+      // Certificate (every column outside the candidates scores at most B) and
+      // the runs of near-equal FP32 scores that reach into the top-k1.
+      if (wid == 0) {
+        for (int c = lane; c < K; c += kWarp) w.need[c] = 0;
+        __syncwarp();
+        bool cert = true;
+        if (K == Kc && sB > -FLT_MAX) cert = double(w.s[w.ord[k1 - 1]]) - eps_r > double(sB) + eps_g;
+        if (lane == 0) {
+          sh[2] = cert ? 1 : 0;
+          int nneed = 0;
+          if (cert) {
+            int r = 0;
+            while (r < K) {
+              int r1 = r;
+              while (r1 + 1 < K && double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r) ++r1;
+              if (r1 > r && r < k1)
+                for (int q = r; q <= r1; ++q) {
+                  w.need[w.ord[q]] = 1;
+                  ++nneed;
+                }
+              r = r1 + 1;
+            }
+          }
+          sh[3] = nneed;
         }
       }
       __syncthreads();
-      if (wid == 0) {
-        if (lane == 0) {
-          if (sh[3]) atomicAdd(reinterpret_cast<unsigned long long*>(io.status + kStFp64), (unsigned long long)sh[3]);
-          // Re-sort each run by (FP64 value desc, index asc).
-          int r = 0;
-          while (r < K) {
-            if (!w.need[w.ord[r]]) {
-              ++r;
-              continue;
-            }
-            int r1 = r;
-            while (r1 + 1 < K && w.need[w.ord[r1 + 1]] &&
-                   double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r)
-              ++r1;
-            for (int a = r + 1; a <= r1; ++a) {
-              const int c = w.ord[a];
-              int b = a;
-              while (b > r && ranks_before(w.t[c], w.idx[c], w.t[w.ord[b - 1]], w.idx[w.ord[b - 1]])) {
-                w.ord[b] = w.ord[b - 1];
-                --b;
-              }
-              w.ord[b] = c;
-            }
-            r = r1 + 1;
+      ok = sh[2] != 0;
+      if (ok) {
+        // FP64 values of the candidates in near-tie runs, one warp each.
+        if (sh[3] > 0) {
+          int seen = 0;
+          for (int c = 0; c < K; ++c) {
+            if (!w.need[c]) continue;
+            if (seen++ % NW != wid) continue;
+            const int j = w.idx[c];
+            double tv = 1.0;
+            if (j != i) tv = dot_fp64_raw(io, i, j, lane) / (io.norm[i] * io.norm[j]);
+            if (lane == 0) w.t[c] = tv;
           }
         }
-        __syncwarp();
-        for (int r = lane; r < k1; r += kWarp) {
-          const int c = w.ord[r];
-          io.knn_idx[size_t(i) * k1 + r] = w.idx[c];
-          io.knn_score[size_t(i) * k1 + r] = w.need[c] ? float(w.t[c]) : w.s[c];
+        __syncthreads();
+        if (wid == 0) {
+          if (lane == 0) {
+            if (sh[3]) atomicAdd(reinterpret_cast<unsigned long long*>(io.status + kStFp64), (unsigned long long)sh[3]);
+            // Re-sort each run by (FP64 value desc, index asc).
+            int r = 0;
+            while (r < K) {
+              if (!w.need[w.ord[r]]) {
+                ++r;
+                continue;
+              }
+              int r1 = r;
+              while (r1 + 1 < K && w.need[w.ord[r1 + 1]] &&
+                     double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r)
+                ++r1;
+              for (int a = r + 1; a <= r1; ++a) {
+                const int c = w.ord[a];
+                int b = a;
+                while (b > r && ranks_before(w.t[c], w.idx[c], w.t[w.ord[b - 1]], w.idx[w.ord[b - 1]])) {
+                  w.ord[b] = w.ord[b - 1];
+                  --b;
+                }
+                w.ord[b] = c;
+              }
+              r = r1 + 1;
+            }
+          }
+          __syncwarp();
+          for (int r = lane; r < k1; r += kWarp) {
+            const int c = w.ord[r];
+            io.knn_idx[size_t(i) * k1 + r] = w.idx[c];
+            io.knn_score[size_t(i) * k1 + r] = w.need[c] ? float(w.t[c]) : w.s[c];
+          }
         }
       }
     }
-  }
-  if (!ok && t == 0) {
-    const int slot = atomicAdd(fb_count, 1);
-    fb_rows[slot] = int32_t(i);
-    atomicAdd(reinterpret_cast<unsigned long long*>(io.status + fb_stat), 1ull);
+    if (!ok && t == 0) {
+      const int slot = atomicAdd(fb_count, 1);
+      fb_rows[slot] = int32_t(i);
+      atomicAdd(reinterpret_cast<unsigned long long*>(io.status + fb_stat), 1ull);
+    }
+    __syncthreads();  // the shared row and lists are reused by the next row
   }
 }
 
@@ -681,6 +687,10 @@ static RowIo make_io(const Shape& sh, const void* xq, const void* xg, const floa
 
 double rescore_eps(int dp) { return (dp / 32 + 10) * kU32 * 1.01; }
 
+// Rows a launch over a gathered row set covers at once (both kernels loop):
+// about one resident wave on 152 SMs.
+constexpr int64_t kGatheredRows = 2048;
+
 // Warps per row of the CTA-per-row refinement (0: warp-per-row kernel).  By
 // default 4 for rows of 1,024 floats or more, where the warp-per-row kernel's
 // register-resident row (64 registers) leaves only 16 warps per SM to cover
@@ -703,7 +713,10 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
                    int32_t* fb_rows, int32_t* fb_count,
                    long long* status, cudaStream_t s, int64_t grid_rows, int fb_stat) {
   RowIo io = make_io(sh, xq, xg, xhat, norm, knn_idx, knn_score, status);
-  const int64_t g = grid_rows > 0 && grid_rows < sh.n ? grid_rows : sh.n;
+  int64_t g = grid_rows > 0 && grid_rows < sh.n ? grid_rows : sh.n;
+  // A gathered row set (size on the device): the kernels loop over it, so one
+  // resident wave of rows is enough.
+  if (rows && count) g = std::min<int64_t>(g, kGatheredRows);
   const unsigned blocks = unsigned((g + WPB - 1) / WPB);
   // First pass: uncertified rows go to the recheck; a recheck's failures go to the exact scan.
   const int stat = fb_stat >= 0 ? fb_stat : ((rows && !part_by_row) ? kStFallback2 : kStFallback);
