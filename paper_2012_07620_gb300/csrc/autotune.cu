@@ -186,7 +186,7 @@ rerank_status rerank_autotune(rerank_ctx* ctx, const void* xq, int64_t nq, const
     //    the refinement, fewer rows left for the recheck
     {
       double t0_best = 1e300;
-      const int m_set[] = {-1, 8, 22, 30};
+      const int m_set[] = {-1, 8, 22, 30, 38};  // 38: the full 64-entry list for k1 = 26
       Tuning base0 = best;
       for (int m : m_set) {
         Tuning t = base0;
