@@ -309,6 +309,16 @@ int launch_scan(const int32_t* in, int64_t n, int64_t* out, cudaStream_t s);
 int launch_scan32(const int32_t* in, int64_t n, int32_t* out, cudaStream_t s);
 int launch_graph(const Shape& sh, const Buffers& b, float alpha, int aggregator, int feature,
                   long long* status, cudaStream_t s);
+// A serving request's graph (A* features) from the resident gallery graph:
+// only rows whose A* row can change (the queries, the touched gallery rows
+// touched[0 .. *n_touched) and the old and new targets of their lists) are
+// built; the others are the resident rows (rst / rln / rcol / rval, gallery
+// indices) shifted by Q.  aff / src: n bytes of scratch each.  Same CSR,
+// message lists and nnz counter as launch_graph.
+int launch_graph_incremental(const Shape& sh, const Buffers& b, int64_t Q, const int32_t* touched,
+                             const int32_t* n_touched, const int32_t* res_knn, const int64_t* rst,
+                             const int32_t* rln, const int32_t* rcol, const float* rval, uint8_t* aff,
+                             uint8_t* src, float alpha, int aggregator, long long* status, cudaStream_t s);
 // Rows of a layer whose output is known elsewhere are copied instead of
 // recomputed (serving: the resident gallery's own layer rows, whose inputs a
 // request left unchanged).  Row i >= shift with changed[i] == 0 copies row

@@ -217,7 +217,8 @@ __global__ void k_mark_h0(int64_t n, int64_t Q, const int64_t* __restrict__ st, 
                           const int32_t* __restrict__ nbr, const float* __restrict__ nbr_w,
                           const int32_t* __restrict__ nbr_n, const int32_t* __restrict__ rnbr,
                           const float* __restrict__ rnbr_w, const int32_t* __restrict__ rnbr_n, int k2p1,
-                          uint8_t* __restrict__ h0chg, uint8_t* __restrict__ msgchg) {
+                          const uint8_t* __restrict__ aff, uint8_t* __restrict__ h0chg,
+                          uint8_t* __restrict__ msgchg) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (i < Q) {
@@ -230,10 +231,12 @@ __global__ void k_mark_h0(int64_t n, int64_t Q, const int64_t* __restrict__ st, 
   bool mc = m != rnbr_n[g];
   for (int q = 0; q < m && !mc; ++q)
     mc = nbr[i * k2p1 + q] != rnbr[g * k2p1 + q] + Q || nbr_w[i * k2p1 + q] != rnbr_w[g * k2p1 + q];
+  // Rows the incremental graph did not rebuild (aff clear) are resident copies.
   const int len = ln[i];
   bool hc = len != rln[g];
   const int64_t a = st[i], ra = rst[g];
-  for (int p = 0; p < len && !hc; ++p) hc = cl[a + p] != rcl[ra + p] + Q || vl[a + p] != rvl[ra + p];
+  if (!aff || aff[i])
+    for (int p = 0; p < len && !hc; ++p) hc = cl[a + p] != rcl[ra + p] + Q || vl[a + p] != rvl[ra + p];
   h0chg[i] = hc ? 1 : 0;
   msgchg[i] = mc ? 1 : 0;
 }
@@ -494,15 +497,24 @@ rerank_status enqueue_request(Server& v, Slot& sl, const rerank_request& rq, cud
   int32_t* fb_i = reinterpret_cast<int32_t*>(fb_s + size_t(sm) * fallback_warps() * fallback_k(sh));
   launch_refine_fallback(sh, dq, dg, b.xhat, b.norm, b.knn_idx, b.knn_score, b.fb2_rows, b.fb2_count, fb_s, fb_i,
                          status, sm, s);
-  // 5. graph, propagation, ranking on X_u
-  launch_graph(sh, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, status, s);
+  // 5. graph, propagation, ranking on X_u.  With the gallery's own graph kept,
+  // only the rows of A* the request can change are built (aff marks them).
+  uint8_t* aff = nullptr;
+  if (v.reuse && ctx->cfg.feature_mode == RERANK_FEAT_ASTAR) {
+    aff = reinterpret_cast<uint8_t*>(b.label);  // 4n bytes, free once the refinement is done
+    const Server::ResLayer& r0 = v.res_layers[0];
+    launch_graph_incremental(sh, b, Q, sl.touched, sl.scal + 1, v.res_knn_idx, r0.start, r0.len, r0.col, r0.val, aff,
+                             aff + n, ctx->cfg.alpha, ctx->cfg.aggregator, status, s);
+  } else {
+    launch_graph(sh, b, ctx->cfg.alpha, ctx->cfg.aggregator, ctx->cfg.feature_mode, status, s);
+  }
   RR_CUDA(cudaMemsetAsync(b.hash_keys_vals, 0, sizeof(float) * size_t(sm) * (size_t(n) + size_t((n + 31) / 32)), s));
   const int k2p1 = v.k2 + 1;
   const unsigned mg = unsigned((n + 255) / 256);
   if (v.reuse) {
     const Server::ResLayer& r0 = v.res_layers[0];
     k_mark_h0<<<mg, 256, 0, s>>>(n, Q, b.start[2], b.len[2], b.col[2], b.val[2], r0.start, r0.len, r0.col, r0.val,
-                                 b.nbr, b.nbr_w, b.nbr_n, v.res_nbr, v.res_nbr_w, v.res_nbr_n, k2p1, sl.chg[0],
+                                 b.nbr, b.nbr_w, b.nbr_n, v.res_nbr, v.res_nbr_w, v.res_nbr_n, k2p1, aff, sl.chg[0],
                                  sl.msgchg);
   }
   int src = 2;
