@@ -120,6 +120,7 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
     b.fb3_count = c.take<int32_t>(4);
   }
   b.row_floor = c.take<int>(size_t(n));
+  b.work = c.take<int32_t>(16);
   b.nb4 = c.take<int32_t>(4 * size_t(n));
   b.label = c.take<int32_t>(size_t(n));
   b.order = c.take<int32_t>(size_t(n));
@@ -288,7 +289,7 @@ rerank_status enqueue_job(rerank_ctx* ctx, const JobRun& j, cudaStream_t s, Stag
       nl += launch_sim_fp32_topk(sh, b.xhat, b.row_floor, b.part_s, b.part_i, ctx->sm_count, s);
     } else {
       const int r = launch_sim_tc_topk(sh, b.xlow, prec == RERANK_PREC_FP8, b.xscale, b.row_floor, b.part_s,
-                                       b.part_i, status, ctx->sm_count, s);
+                                       b.part_i, status, ctx->sm_count, s, b.work);
       if (r < 0) return RERANK_ECUDA;
       nl += r;
     }

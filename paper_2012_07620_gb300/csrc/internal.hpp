@@ -119,6 +119,7 @@ struct Buffers {
   int32_t* csc_row = nullptr;
   float* csc_val = nullptr;
   uint32_t* rank_scratch = nullptr;
+  int32_t* work = nullptr;       // 16: item counter of the similarity kernel
   // dense features (RERANK_FEAT_X)
   float* hd[2] = {nullptr, nullptr};  // np x dp each, alternating layers
   double* hinv = nullptr;             // np: 1 / ||h_i^(L)||
@@ -226,8 +227,10 @@ int launch_gather_rows(const int32_t* rows, const int32_t* count, const __nv_bfl
 // a row share their K-th best score.
 int launch_sim_fp32_topk(const Shape& sh, const float* xhat, int* row_floor, float* part_s, int32_t* part_i,
                          int sm_count, cudaStream_t s);
+// work (4 bytes, nullable): counter for the dynamic item order of the main pass.
 int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float* inv_scale, int* row_floor,
-                       float* part_s, int32_t* part_i, long long* status, int sm_count, cudaStream_t s);
+                       float* part_s, int32_t* part_i, long long* status, int sm_count, cudaStream_t s,
+                       int32_t* work = nullptr);
 // Rectangular block: rows of `a` (a_rows of them, vertices row0 ..) against the
 // columns of `b` (b_cols, vertices col0 ..); per row P lists of its best K
 // columns (vertex indices) in part_s/part_i [a_rows][P][K].  Rows and columns

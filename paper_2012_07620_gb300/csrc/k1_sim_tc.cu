@@ -73,9 +73,14 @@ struct alignas(1024) TcSmemT {
   uint64_t tfull[2];
   uint64_t tempty[2];
   uint64_t done;
+  // Dynamic item order: the publisher's ring of item numbers.
+  int item_q[4];
+  uint64_t ifull[4];
+  uint64_t iempty[4];
   uint32_t tmem_base;
   int abort;
 };
+constexpr int IQ = 4;  // item ring depth
 constexpr int PAIR_STAGES = 6;
 using TcSmem = TcSmemT<STAGES, B_BYTES>;
 using TcSmemPair = TcSmemT<PAIR_STAGES, B_BYTES / 2>;
@@ -116,6 +121,7 @@ struct TcArgs {
   long long* status;
   const TcInst* insts;      // batched launch: the instances (device memory), else null
   int ninst, items_total;
+  int* work;                // non-null: items are taken in order from this counter (zero at launch)
 };
 
 // One work item (a row block against a chunk of column tiles) with the
@@ -223,6 +229,55 @@ __device__ __forceinline__ void drain_delay() {
   for (int k = 0; k < 200; ++k) __nanosleep(1000);
 }
 
+// Item order.  Static: unit, unit + units, ...  Dynamic (A.work set): the
+// publisher (the TMA thread of a CTA, or of the even CTA of a pair) takes the
+// next item number from the global counter and hands it to every consumer of
+// the work through a ring in shared memory (both CTAs' rings for a pair):
+// the MMA thread, the epilogue warps and, in the odd CTA of a pair, its TMA
+// thread.  A slot is reused once all consumers released it on the even CTA's
+// `iempty`.  Items still come in increasing order overall, but a unit that
+// finishes early takes more of them, which evens out the per-item cost of the
+// top-K epilogue.  Every consumer reads the same sequence; the first number
+// >= items ends it.
+struct ItemRing {
+  uint32_t qs = 0, qph = 0;
+};
+
+template <bool PAIR, class Smem>
+__device__ __forceinline__ int next_item(Smem& sm, const TcArgs& A, bool publisher, bool leader, int prev, int unit,
+                                         int units, ItemRing& rg, volatile int* abort, bool& ok) {
+  if (!A.work) return prev < 0 ? unit : prev + units;
+  int it = INT_MAX;
+  if (publisher) {
+    it = atomicAdd(A.work, 1);
+    if (!tc::mbar_wait(&sm.iempty[rg.qs], rg.qph ^ 1u, abort, WAIT_LIMIT)) {
+      ok = false;
+      return INT_MAX;
+    }
+    reinterpret_cast<volatile int*>(sm.item_q)[rg.qs] = it;
+    if (PAIR) {
+      tc::st_cluster(tc::map_to_rank(&sm.item_q[rg.qs], 1), it);
+      tc::mbar_arrive_cluster(tc::map_to_rank(&sm.ifull[rg.qs], 1));
+    }
+    tc::mbar_arrive(&sm.ifull[rg.qs]);
+  } else {
+    const bool got = PAIR ? tc::mbar_wait_cluster(&sm.ifull[rg.qs], rg.qph, abort, WAIT_LIMIT)
+                          : tc::mbar_wait(&sm.ifull[rg.qs], rg.qph, abort, WAIT_LIMIT);
+    if (!got) {
+      ok = false;
+      return INT_MAX;
+    }
+    it = reinterpret_cast<volatile int*>(sm.item_q)[rg.qs];
+    if (PAIR && !leader) tc::mbar_arrive_cluster(tc::map_to_rank(&sm.iempty[rg.qs], 0));
+    else tc::mbar_arrive(&sm.iempty[rg.qs]);
+  }
+  if (++rg.qs == IQ) {
+    rg.qs = 0;
+    rg.qph ^= 1u;
+  }
+  return it;
+}
+
 // PAIR: the CTAs of a cluster of two compute 256-row tiles together with
 // tcgen05 cta_group::2.  The even CTA ("leader") issues the MMAs; each CTA
 // loads its own 128 rows of A and its 128 of the tile's 256 B rows, counted
@@ -259,6 +314,12 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
       tc::mbar_init(&sm.tempty[b], 4 * EGROUPS * (PAIR ? 2 : 1));
     }
     tc::mbar_init(&sm.done, 1);
+    for (int q = 0; q < IQ; ++q) {
+      tc::mbar_init(&sm.ifull[q], 1);
+      // consumers: the MMA thread and the epilogue warps; for a pair also the
+      // odd CTA's TMA thread and epilogue warps (they release on the even CTA's)
+      tc::mbar_init(&sm.iempty[q], PAIR ? 2 + 8 * EGROUPS : 1 + 4 * EGROUPS);
+    }
     sm.abort = 0;
     tc::fence_barrier_init();
     if (!BATCH) {
@@ -292,7 +353,11 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
       uint32_t armed = 0;  // bit s: slot s holds a load that may still be in flight
       uint32_t armed_phase = 0;
       bool ok = true;
-      for (int item = unit; item < items && ok && !A.stall; item += units) {
+      ItemRing rg;
+      const bool publisher = !PAIR || leader;
+      for (int item = A.stall ? INT_MAX : next_item<PAIR>(sm, A, publisher, leader, -1, unit, units, rg, abort, ok);
+           item < items && ok;
+           item = next_item<PAIR>(sm, A, publisher, leader, item, unit, units, rg, abort, ok)) {
         TcItem it;
         get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
         const int rb = it.rb;
@@ -347,7 +412,9 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
       constexpr uint16_t both = 3;
       uint32_t stage = 0, phase = 0, tcount = 0;
       bool ok = true;
-      for (int item = unit; item < items && ok; item += units) {
+      ItemRing rg;
+      for (int item = next_item<PAIR>(sm, A, false, leader, -1, unit, units, rg, abort, ok); item < items && ok;
+           item = next_item<PAIR>(sm, A, false, leader, item, unit, units, rg, abort, ok)) {
         TcItem it;
         get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
         const int kb_total = it.kblocks * SEGS;
@@ -419,7 +486,18 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
     // score keeps the earlier, lower column in front (score desc, column asc).
     float ls[KL];
     int li[KL];
-    for (int item = unit; item < items && ok; item += units) {
+    ItemRing rg;
+    // one lane of the warp takes the item from the ring, the warp shares it
+    auto take = [&](int prev) {
+      int v = 0;
+      bool good = true;
+      if (lane == 0) v = next_item<PAIR>(sm, A, false, leader, prev, unit, units, rg, abort, good);
+      v = __shfl_sync(kFull, v, 0);
+      good = __shfl_sync(kFull, good ? 1 : 0, 0) != 0;
+      if (!good) ok = false;
+      return v;
+    };
+    for (int item = take(-1); item < items && ok; item = take(item)) {
       TcItem it;
       get_item<BATCH>(A, pA0, pA1, pB0, pB1, bmaps, row_blocks, nrows, item, it, chunks);
       const int chunk = it.chunk;
@@ -737,6 +815,15 @@ bool tc_pairs() {
   return on != 0;
 }
 int tc_item_rows() { return tc_pairs() ? 2 * TBM : TBM; }
+// Whether the main pass takes its items dynamically (see next_item);
+// RERANK_TC_DYNAMIC=0 selects the static order (identical lists).
+bool tc_dynamic() {
+  static const int on = [] {
+    const char* e = std::getenv("RERANK_TC_DYNAMIC");
+    return (e && e[0] == '0') ? 0 : 1;
+  }();
+  return on != 0;
+}
 int tc_lists_per_chunk(int dp, int segs) { return dp * segs <= 1024 ? 2 : 1; }
 static_assert(sizeof(TcSmem) + 1024 <= 227 * 1024, "shared memory of the tensor-core kernel");
 int tc_kmax() { return KLIST; }
@@ -746,7 +833,8 @@ int tc_tile_cols() { return TBN; }
 // Returns the number of kernels launched (1), or a negative value when the
 // tensor map cannot be encoded.
 int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float* inv_scale, int* row_floor,
-                       float* part_s, int32_t* part_i, long long* status, int sm_count, cudaStream_t s) {
+                       float* part_s, int32_t* part_i, long long* status, int sm_count, cudaStream_t s,
+                       int32_t* work) {
   CUtensorMap map;
   if (!make_map(&map, xlow, sh.np, sh.dp, fp8)) return -1;
   cudaMemsetAsync(row_floor, kFloorResetByte, sizeof(int) * size_t(sh.n), s);
@@ -767,6 +855,10 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   A.part_i = part_i;
   A.status = status;
   A.stall = stall_hook();
+  if (work && tc_dynamic()) {
+    cudaMemsetAsync(work, 0, sizeof(int32_t), s);
+    A.work = work;
+  }
   const int items = A.row_blocks * A.chunks;
   if (pairs) {
     const bool ok = fp8 ? launch_mode_pair<MODE_FP8>(map, map, A, eg, items, sm_count, s)

@@ -694,14 +694,14 @@ constexpr int64_t kGatheredRows = 2048;
 // Warps per row of the CTA-per-row refinement (0: warp-per-row kernel).  By
 // default 4 for rows of 1,024 floats or more, where the warp-per-row kernel's
 // register-resident row (64 registers) leaves only 16 warps per SM to cover
-// the candidate gathers; RERANK_REFINE_CTA = 0, 4 or 8 forces a choice
-// (identical results).
+// the candidate gathers; RERANK_REFINE_CTA = 0, 2, 4 or 8 forces a choice
+// (identical results); 2 is also accepted.
 static int refine_cta_warps(int dp) {
   static const int forced = [] {
     const char* e = std::getenv("RERANK_REFINE_CTA");
     if (!e) return -1;
     const int x = std::atoi(e);
-    return (x == 4 || x == 8) ? x : 0;
+    return (x == 2 || x == 4 || x == 8) ? x : 0;
   }();
   if (forced >= 0) return forced;
   return dp >= 1024 ? 4 : 0;
@@ -722,7 +722,11 @@ int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* 
   const int stat = fb_stat >= 0 ? fb_stat : ((rows && !part_by_row) ? kStFallback2 : kStFallback);
   if (refine_cta_warps(sh.dp) > 0) {
     const size_t smem = size_t(sh.dp) * 4;
-    if (refine_cta_warps(sh.dp) == 8)
+    if (refine_cta_warps(sh.dp) == 2)
+      k2_refine_cta<2><<<unsigned(g), 2 * kWarp, smem, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em,
+                                                             rescore_eps(sh.dp), rows, count, part_by_row, fb_rows,
+                                                             fb_count, stat);
+    else if (refine_cta_warps(sh.dp) == 8)
       k2_refine_cta<8><<<unsigned(g), 8 * kWarp, smem, s>>>(io, sh.n, part_s, part_i, P, sh.K, sh.k1, em,
                                                              rescore_eps(sh.dp), rows, count, part_by_row, fb_rows,
                                                              fb_count, stat);
