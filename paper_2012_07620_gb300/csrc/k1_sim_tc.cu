@@ -62,12 +62,17 @@ enum { MODE_BF16 = 0, MODE_FP8 = 1, MODE_SPLIT = 2, MODE_GATHER = 3 };
 __host__ __device__ constexpr bool gathered(int mode) { return mode == MODE_SPLIT || mode == MODE_GATHER; }
 
 // Shared memory of one CTA.  A CTA of a pair holds only its half of the B
-// rows (128 of the tile's 256), so the same space holds more stages.
-template <int STG, int BBYTES>
+// rows (128 of the tile's 256), so the same space holds more stages.  EGN
+// epilogue groups; QC > 0: each row's queue of QC admitted (score, column)
+// pairs not yet in its list (paired kernels).
+template <int STG, int BBYTES, int EGN, int QC>
 struct alignas(1024) TcSmemT {
+  static constexpr int kStages = STG;
   uint8_t a[STG][A_BYTES];
   uint8_t b[STG][BBYTES];
-  float batch[EG_MAX][32][TBM];  // per group: scores of the 32 columns being folded in
+  float batch[EGN][32][TBM];  // per group: scores of the 32 columns being folded in
+  float qsc[QC > 0 ? EGN : 1][QC > 0 ? QC : 1][TBM];
+  int32_t qcol[QC > 0 ? EGN : 1][QC > 0 ? QC : 1][TBM];
   uint64_t full[STG];
   uint64_t empty[STG];
   uint64_t tfull[2];
@@ -81,11 +86,13 @@ struct alignas(1024) TcSmemT {
   int abort;
 };
 constexpr int IQ = 4;  // item ring depth
-constexpr int PAIR_STAGES = 6;
-using TcSmem = TcSmemT<STAGES, B_BYTES>;
-using TcSmemPair = TcSmemT<PAIR_STAGES, B_BYTES / 2>;
-template <bool PAIR>
-using SmemOf = typename std::conditional<PAIR, TcSmemPair, TcSmem>::type;
+constexpr int QCAP = 8;  // entries of a row's insertion queue (paired kernels)
+using TcSmem = TcSmemT<STAGES, B_BYTES, EG_MAX, 0>;
+// Pairs: 32 KB stages; six of them with one epilogue group, five with two.
+template <int EG>
+using TcSmemPair = TcSmemT<EG == 1 ? 6 : 5, B_BYTES / 2, EG, QCAP>;
+template <bool PAIR, int EG>
+using SmemOf = typename std::conditional<PAIR, TcSmemPair<EG>, TcSmem>::type;
 
 // Batched launches: up to kMaxBatchInst instances, each a matrix against
 // itself; their tensor maps travel as one kernel parameter.
@@ -229,6 +236,24 @@ __device__ __forceinline__ void drain_delay() {
   for (int k = 0; k < 200; ++k) __nanosleep(1000);
 }
 
+// Insert (cs, ci) into a row's sorted list: slot j takes cs where cs first
+// beats ls[j], and slot j-1's old entry for every later slot.  For the sorted
+// scores that is max(min(ls[j-1], cs), ls[j]); the columns follow the same
+// choice.  All tests use the old list: no serial dependency.  Columns arrive
+// in increasing order, so an equal score keeps the earlier, lower column in
+// front (score desc, column asc); cs = -inf changes nothing.
+template <int KL>
+__device__ __forceinline__ void list_insert(float (&ls)[KL], int (&li)[KL], float cs, int ci) {
+#pragma unroll
+  for (int j = KL - 1; j > 0; --j) {
+    const bool bj = cs > ls[j], bp = cs > ls[j - 1];
+    li[j] = bp ? li[j - 1] : (bj ? ci : li[j]);
+    ls[j] = fmaxf(fminf(ls[j - 1], cs), ls[j]);
+  }
+  li[0] = cs > ls[0] ? ci : li[0];
+  ls[0] = fmaxf(cs, ls[0]);
+}
+
 // Item order.  Static: unit, unit + units, ...  Dynamic (A.work set): the
 // publisher (the TMA thread of a CTA, or of the even CTA of a pair) takes the
 // next item number from the global counter and hands it to every consumer of
@@ -287,8 +312,9 @@ __device__ __forceinline__ int next_item(Smem& sm, const TcArgs& A, bool publish
 template <int MODE, int KL, int EGROUPS, bool BATCH, bool PAIR>
 __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMap* pA1, const CUtensorMap* pB0,
                                         const CUtensorMap* pB1, const CUtensorMap* bmaps, const TcArgs& A) {
-  using Smem = SmemOf<PAIR>;
-  constexpr int STG = PAIR ? PAIR_STAGES : STAGES;
+  using Smem = SmemOf<PAIR, EGROUPS>;
+  constexpr int STG = Smem::kStages;
+  constexpr bool QUEUE = PAIR;  // insertion queues (see the epilogue)
   constexpr int ROWS = PAIR ? 2 * TBM : TBM;  // A rows of one work item
   extern __shared__ uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -486,6 +512,29 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
     // score keeps the earlier, lower column in front (score desc, column asc).
     float ls[KL];
     int li[KL];
+    // Paired kernels queue a row's admitted columns in shared memory and fold
+    // them into the list only when some row's queue would overflow or the
+    // item ends: a warp pays, per drain, the largest count among its 32 rows,
+    // and that maximum is far smaller over many batches than summed batch by
+    // batch (a warm row admits ~0.3 columns per batch).  Columns still enter
+    // a list in increasing order.
+    int qn = 0;
+    auto drain_queue = [&]() {
+      int rq = qn;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rq = max(rq, __shfl_xor_sync(kFull, rq, o));
+#pragma unroll 1
+      for (int rd = 0; rd < rq; ++rd) {
+        float cs = -INFINITY;
+        int ci = kInvalidIdx;
+        if (rd < qn) {
+          cs = sm.qsc[QUEUE ? eg : 0][rd][r];
+          ci = sm.qcol[QUEUE ? eg : 0][rd][r];
+        }
+        list_insert<KL>(ls, li, cs, ci);
+      }
+      qn = 0;
+    };
     ItemRing rg;
     // one lane of the warp takes the item from the ring, the warp shares it
     auto take = [&](int prev) {
@@ -509,6 +558,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
         ls[j] = -FLT_MAX;
         li[j] = kInvalidIdx;
       }
+      qn = 0;
       // Admission: beat the last slot and reach the row's floor (s >= floor,
       // i.e. s > the float below it).  The floor is the best K-th score any
       // chunk of this row has published: chunks publish their running K-th
@@ -556,6 +606,30 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
             mask |= (sc > thr) ? (1u << j) : 0u;
           }
           int rounds = __popc(mask);
+          if constexpr (QUEUE) {
+            if (__any_sync(kFull, qn + rounds > QCAP)) {
+              // No room: empty the queues, then fold this batch in directly,
+              // tested again against the raised lists.
+              drain_queue();
+              const float thr2 = fmaxf(ls[KL - 1], floor_below);
+              uint32_t keep = 0;
+              for (uint32_t mm = mask; mm; mm &= mm - 1u) {
+                const int j = __ffs(mm) - 1;
+                if (sm.batch[eg][j][r] > thr2) keep |= 1u << j;
+              }
+              mask = keep;
+              rounds = __popc(mask);
+            } else {
+              while (mask) {
+                const int j = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                sm.qsc[QUEUE ? eg : 0][qn][r] = sm.batch[eg][j][r];
+                sm.qcol[QUEUE ? eg : 0][qn][r] = int(cbase + j);
+                ++qn;
+              }
+              rounds = 0;
+            }
+          }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(kFull, rounds, o));
 #pragma unroll 1
@@ -568,18 +642,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
               cs = sm.batch[eg][j][r];
               ci = int(cbase + j);
             }
-            // Insert (cs, ci): slot j takes cs where cs first beats ls[j], and
-            // slot j-1's old entry for every later slot.  For the sorted scores
-            // that is max(min(ls[j-1], cs), ls[j]); the columns follow the same
-            // choice.  All tests use the old list: no serial dependency.
-#pragma unroll
-            for (int j = KL - 1; j > 0; --j) {
-              const bool bj = cs > ls[j], bp = cs > ls[j - 1];
-              li[j] = bp ? li[j - 1] : (bj ? ci : li[j]);
-              ls[j] = fmaxf(fminf(ls[j - 1], cs), ls[j]);
-            }
-            li[0] = cs > ls[0] ? ci : li[0];
-            ls[0] = fmaxf(cs, ls[0]);
+            list_insert<KL>(ls, li, cs, ci);
           }
         }
         tc::tc_fence_before();
@@ -606,6 +669,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
         }
       }
       if (!ok) break;
+      if (QUEUE) drain_queue();
       if (live) {
         const size_t o = ((size_t(arow) * it.chunks + chunk) * EGROUPS + eg) * it.K;
         // The K-th best as a running minimum over the first K slots (the list
@@ -717,7 +781,7 @@ template <int MODE, int KL, int EG>
 int pair_units(int sm_count) {
   static int cached = -1;
   if (cached < 0) {
-    const size_t smem = sizeof(TcSmemPair) + 1024;
+    const size_t smem = sizeof(TcSmemPair<EG>) + 1024;
     cudaFuncSetAttribute(k1_tc2_topk<MODE, KL, EG>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(unsigned(sm_count & ~1));
@@ -745,7 +809,7 @@ bool launch_kl_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A,
                     cudaStream_t s) {
   const int units = pair_units<MODE, KL, EG>(sm_count);
   if (units < 1) return false;
-  const size_t smem = sizeof(TcSmemPair) + 1024;
+  const size_t smem = sizeof(TcSmemPair<EG>) + 1024;
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(unsigned(2 * (items < units ? items : units)));
   cfg.blockDim = dim3(threads_of(EG));
@@ -804,7 +868,8 @@ __global__ void k_gather_rows(const int32_t* __restrict__ rows, const int32_t* _
 }  // namespace
 
 size_t tc_smem_bytes() { return sizeof(TcSmem) + 1024; }
-static_assert(sizeof(TcSmemPair) + 1024 <= 227 * 1024, "shared memory of the paired tensor-core kernel");
+static_assert(sizeof(TcSmemPair<1>) + 1024 <= 227 * 1024, "shared memory of the paired tensor-core kernel");
+static_assert(sizeof(TcSmemPair<2>) + 1024 <= 227 * 1024, "shared memory of the paired tensor-core kernel");
 // Whether the main similarity pass runs on CTA pairs (cta_group::2).  Both
 // kernels give identical lists; RERANK_TC_PAIRS=0 selects the single-CTA one.
 bool tc_pairs() {

@@ -432,6 +432,62 @@ __device__ void rank_cands(WarpSmem& w, int n, int lane) {
   __syncwarp();
 }
 
+// Merge of the P sorted candidate lists of a row by all threads of a CTA
+// (the lists staged in shared memory, P * K <= MERGE_CAP): an entry's place in
+// the merged order is its position in its own list plus, for every other
+// list, the number of entries there that rank before it (a binary search;
+// the lists are disjoint and sorted by (score desc, index asc)).  Entries
+// ranked below K are dropped.  Same result as merge_lists.
+constexpr int MERGE_CAP = 512;
+struct MergeSmem {
+  float s[MERGE_CAP];
+  int32_t i[MERGE_CAP];
+  int len[32];
+};
+
+__device__ int merge_lists_cta(WarpSmem& w, MergeSmem& m, const float* ls, const int32_t* li, int P, int K,
+                               int64_t n, int t, int nthreads, float& B) {
+  for (int e = t; e < P * K; e += nthreads) {
+    m.s[e] = ls[e];
+    m.i[e] = li[e];
+  }
+  __syncthreads();
+  if (t < P) {
+    // An index outside [0, n) ends its list (see merge_lists).
+    int L = 0;
+    while (L < K && m.i[t * K + L] >= 0 && m.i[t * K + L] < n) ++L;
+    m.len[t] = L;
+  }
+  __syncthreads();
+  for (int e = t; e < P * K; e += nthreads) {
+    const int p = e / K, i = e - p * K;
+    if (i >= m.len[p]) continue;
+    const float sc = m.s[e];
+    const int32_t ic = m.i[e];
+    int rank = i;
+    for (int q = 0; q < P && rank < K; ++q) {
+      if (q == p) continue;
+      int lo = 0, hi = m.len[q];
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ranks_before(m.s[q * K + mid], m.i[q * K + mid], sc, ic)) lo = mid + 1;
+        else hi = mid;
+      }
+      rank += lo;
+    }
+    if (rank < K) {
+      w.idx[rank] = ic;
+      w.g[rank] = sc;
+    }
+  }
+  int total = 0;
+  for (int q = 0; q < P; ++q) total += m.len[q];
+  __syncthreads();
+  const int cnt = total < K ? total : K;
+  B = cnt == K ? w.g[K - 1] : -FLT_MAX;
+  return cnt;
+}
+
 // Two FP32 dot products of row i (in shared memory) with candidate rows: lane
 // l's FMA chain over float4s l, l + 32, ... and the warp tree, as dot2_fp32
 // and dot4_reg, so the values are identical to theirs.
@@ -465,6 +521,7 @@ k2_refine_cta(RowIo io, int64_t n, const float* __restrict__ part_s, const int32
               int fb_stat) {
   extern __shared__ float4 own[];  // dp / 4 float4: row i
   __shared__ WarpSmem w;
+  __shared__ MergeSmem msm;
   __shared__ float sB;
   __shared__ int sh[4];            // [0] candidates, [1] next batch end (-1: done), [2] certified, [3] FP64 count
   const int t = threadIdx.x, wid = t >> 5, lane = t & 31;
@@ -474,13 +531,18 @@ k2_refine_cta(RowIo io, int64_t n, const float* __restrict__ part_s, const int32
     const double eps_g = row_eps_g(em, i);
     const float4* xi4 = reinterpret_cast<const float4*>(io.xhat + size_t(i) * io.dp);
     for (int q = t; q < io.dp / 4; q += NW * kWarp) own[q] = __ldg(xi4 + q);
-    if (wid == 0) {
+    {
       float B = -FLT_MAX;
       const size_t base = size_t(part_by_row ? i : f) * P * Kmax;
       const bool aborted = (io.status[kStErr] & kErrTimeout) != 0;
-      const int cnt = aborted ? 0 : merge_lists(w, part_s + base, part_i + base, P, Kmax, n, lane, B);
+      int cnt = 0;
+      if (!aborted && P * Kmax <= MERGE_CAP) {
+        cnt = merge_lists_cta(w, msm, part_s + base, part_i + base, P, Kmax, n, t, NW * kWarp, B);
+      } else if (!aborted && wid == 0) {
+        cnt = merge_lists(w, part_s + base, part_i + base, P, Kmax, n, lane, B);
+      }
       if (cnt == n) B = -FLT_MAX;  // every column is a candidate
-      if (lane == 0) {
+      if (t == 0) {
         sh[0] = cnt;
         sB = B;
       }
@@ -509,10 +571,18 @@ k2_refine_cta(RowIo io, int64_t n, const float* __restrict__ part_s, const int32
       int K = tmin(Kc, (k1 + 7) & ~3);
       rescore(0, K);
       for (;;) {
-        if (wid == 0) {
-          rank_cands(w, K, lane);
+        // rank of every rescored candidate (all threads), then the stop test
+        for (int c = t; c < K; c += NW * kWarp) {
+          const float sc = w.s[c];
+          const int ic = w.idx[c];
+          int r = 0;
+          for (int e = 0; e < K; ++e) r += ranks_before(w.s[e], w.idx[e], sc, ic) ? 1 : 0;
+          w.ord[r] = c;
+        }
+        __syncthreads();
+        if (t == 0) {
           const bool more = K < Kc && !(double(w.s[w.ord[k1 - 1]]) - 3.0 * eps_r > double(w.g[K]) + eps_g);
-          if (lane == 0) sh[1] = more ? tmin(Kc, K + 8) : -1;
+          sh[1] = more ? tmin(Kc, K + 8) : -1;
         }
         __syncthreads();
         const int K2 = sh[1];
@@ -523,26 +593,37 @@ k2_refine_cta(RowIo io, int64_t n, const float* __restrict__ part_s, const int32
       // Certificate (every column outside the candidates scores at most B) and
       // the runs of near-equal FP32 scores that reach into the top-k1.
       if (wid == 0) {
-        for (int c = lane; c < K; c += kWarp) w.need[c] = 0;
-        __syncwarp();
         bool cert = true;
         if (K == Kc && sB > -FLT_MAX) cert = double(w.s[w.ord[k1 - 1]]) - eps_r > double(sB) + eps_g;
+        // Runs of near-equal FP32 scores that reach into the top-k1, in
+        // parallel: bit q of `gap` says sorted positions q and q + 1 are within
+        // 2 eps_r; q is in a run when bit q - 1 or bit q is set, and the run
+        // reaches into the top-k1 when q < k1 or bits k1 - 1 .. q - 1 are all
+        // set (K <= 64: each lane takes positions lane and lane + 32).
+        const int q0 = lane, q1 = lane + kWarp;
+        const bool f0 = q0 + 1 < K && double(w.s[w.ord[q0]]) - double(w.s[w.ord[q0 + 1]]) <= 2.0 * eps_r;
+        const bool f1 = q1 + 1 < K && double(w.s[w.ord[q1]]) - double(w.s[w.ord[q1 + 1]]) <= 2.0 * eps_r;
+        const uint64_t gap = uint64_t(__ballot_sync(kFull, f0)) | (uint64_t(__ballot_sync(kFull, f1)) << 32);
+        int nneed = 0;
+  #pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = h ? q1 : q0;
+          if (q < K) {
+            const bool inrun = ((gap >> q) & 1ull) || (q > 0 && ((gap >> (q - 1)) & 1ull));
+            bool nd = inrun;
+            if (q >= k1 && inrun) {
+              const int span = q - (k1 - 1);  // bits k1 - 1 .. q - 1
+              const uint64_t want = span >= 64 ? ~0ull : ((1ull << span) - 1ull);
+              nd = ((gap >> (k1 - 1)) & want) == want;
+            }
+            nd = nd && cert;
+            w.need[w.ord[q]] = nd ? 1 : 0;
+            nneed += nd ? 1 : 0;
+          }
+        }
+        nneed = warp_sum(nneed);
         if (lane == 0) {
           sh[2] = cert ? 1 : 0;
-          int nneed = 0;
-          if (cert) {
-            int r = 0;
-            while (r < K) {
-              int r1 = r;
-              while (r1 + 1 < K && double(w.s[w.ord[r1]]) - double(w.s[w.ord[r1 + 1]]) <= 2.0 * eps_r) ++r1;
-              if (r1 > r && r < k1)
-                for (int q = r; q <= r1; ++q) {
-                  w.need[w.ord[q]] = 1;
-                  ++nneed;
-                }
-              r = r1 + 1;
-            }
-          }
           sh[3] = nneed;
         }
       }
