@@ -773,9 +773,10 @@ double rescore_eps(int dp) { return (dp / 32 + 10) * kU32 * 1.01; }
 constexpr int64_t kGatheredRows = 2048;
 
 // Warps per row of the CTA-per-row refinement (0: warp-per-row kernel).  By
-// default 4 for rows of 1,024 floats or more, where the warp-per-row kernel's
-// register-resident row (64 registers) leaves only 16 warps per SM to cover
-// the candidate gathers; RERANK_REFINE_CTA = 0, 2, 4 or 8 forces a choice
+// default 4 for rows of 512 floats or more, where the warp-per-row kernel's
+// register-resident row (16 to 64 registers) leaves too few warps per SM to
+// cover the candidate gathers (measured: 0.69 against 1.07 ms at d = 2048,
+// 0.74 against 0.80 ms at d = 512); RERANK_REFINE_CTA = 0, 2, 4 or 8 forces a choice
 // (identical results); 2 is also accepted.
 static int refine_cta_warps(int dp) {
   static const int forced = [] {
@@ -785,7 +786,7 @@ static int refine_cta_warps(int dp) {
     return (x == 2 || x == 4 || x == 8) ? x : 0;
   }();
   if (forced >= 0) return forced;
-  return dp >= 1024 ? 4 : 0;
+  return dp >= 512 ? 4 : 0;
 }
 
 int launch_refine(const Shape& sh, const void* xq, const void* xg, const float* xhat, const double* norm,
