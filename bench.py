@@ -248,9 +248,10 @@ def _config(args, w):
 
 # DRAM bytes (read + write) of one similarity launch, from `ncu --set full` captures
 # of the current kernel (profiles/); None where no capture of it exists.
-SIM_TRAFFIC_BYTES = {}
-# DRAM bytes of the refinement's first pass, same source.
-REFINE_DRAM_BYTES = {}
+SIM_TRAFFIC_BYTES = {("bf16", "market"): 340.7e6}  # profiles/k1_tc2_topk_bf16_market_23k_d2048.md
+# DRAM bytes of the refinement's first pass, same source
+# (profiles/k2_refine_cta_bf16_market_23k_d2048.md).
+REFINE_DRAM_BYTES = {("bf16", "market"): 1.725e9}
 
 
 def _stage_rooflines(precision, stages, nq, ng, d, k1, k2, rescore_m, h_nnz, layers, workload):
@@ -326,14 +327,15 @@ def _tune(rerank, local, precision, xq, xg, k1, k2, L, path):
 
 
 def _time_instance(rerank, local, precision, xq, xg, k1, k2, L, steps, warmup, stream, flush, tune_path,
-                   world=1):
+                   world=1, feature="astar"):
     """CUDA-event time of `steps` re-ranks (after `warmup`), L2 flushed before
     each; per-stage times from the library's own events.  Returns a dict."""
     import torch
     nq, ng = xq.shape[0], xg.shape[0]
     out_i = torch.empty((nq, ng), dtype=torch.int32, device=xq.device)
     out_d = torch.empty((nq, ng), dtype=torch.float32, device=xq.device)
-    R = rerank.Reranker(device=local, precision=precision, stage_timing=True, autotune_path=tune_path)
+    R = rerank.Reranker(device=local, precision=precision, stage_timing=True, autotune_path=tune_path,
+                        feature=feature)
     for _ in range(warmup):
         R.run(xq, xg, k1, k2, L, 0, out_i, out_d, stream)
     launches = R.last_info()["kernel_launches"]
@@ -695,6 +697,14 @@ def run_ours(args, world, rank, local):
             r["clocks"] = ck.summary()
             r[f"speedup_of_{args.precision}"] = r["ms"] / ms
             line[f"{prec}_path"] = r
+        # Dense x_i initial features (Table 1, first column) on the same instance:
+        # dense layers, final cosines over d (2 Q G d flop) and a radix ranking.
+        with ClockSampler(local) as ck:
+            r = _time_instance(rerank, local, args.precision, xq, xg, k1, k2, L, max(1, min(args.steps, 5)),
+                               args.warmup, stream, flush, tune_path, feature="x")
+        r["clocks"] = ck.summary()
+        r["final_cosines_tflop"] = 2.0 * nq * ng * d / 1e12
+        line["x_features"] = r
     del xq, xg
     torch.cuda.empty_cache()
     if extras and args.workload == "market":

@@ -326,7 +326,7 @@ __device__ __forceinline__ void tc_body(const CUtensorMap* pA0, const CUtensorMa
   const int unit = PAIR ? int(blockIdx.x >> 1) : int(blockIdx.x);   // cluster (pair) or CTA
   const int units = PAIR ? int(gridDim.x >> 1) : int(gridDim.x);
   const int64_t nrows = gathered(MODE) ? int64_t(*A.count) : A.a_rows;
-  const int row_blocks = gathered(MODE) ? int((nrows + TBM - 1) / TBM) : A.row_blocks;
+  const int row_blocks = gathered(MODE) ? int((nrows + ROWS - 1) / ROWS) : A.row_blocks;
   const int chunks = gathered(MODE) ? pick_chunks(row_blocks, A.chunks, A.col_tiles, units) : A.chunks;
   const int items = BATCH ? A.items_total : row_blocks * chunks;
 
@@ -721,8 +721,9 @@ k1_tc_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUte
 // MMA per k-step for both SMs.
 template <int MODE, int KL, int EGROUPS>
 __global__ void __launch_bounds__(threads_of(EGROUPS), 1)
-k1_tc2_topk(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB, TcArgs A) {
-  tc_body<MODE, KL, EGROUPS, false, true>(&mA, &mA, &mB, &mB, nullptr, A);
+k1_tc2_topk(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+            const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs A) {
+  tc_body<MODE, KL, EGROUPS, false, true>(&mA0, &mA1, &mB0, &mB1, nullptr, A);
 }
 
 // Many instances in one persistent launch: the items of all instances form one
@@ -805,8 +806,8 @@ int pair_units(int sm_count) {
 }
 
 template <int MODE, int KL, int EG>
-bool launch_kl_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A, int items, int sm_count,
-                    cudaStream_t s) {
+bool launch_kl_pair(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
+                    const TcArgs& A, int items, int sm_count, cudaStream_t s) {
   const int units = pair_units<MODE, KL, EG>(sm_count);
   if (units < 1) return false;
   const size_t smem = sizeof(TcSmemPair<EG>) + 1024;
@@ -822,17 +823,19 @@ bool launch_kl_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A,
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k1_tc2_topk<MODE, KL, EG>, a, b, A) == cudaSuccess;
+  return cudaLaunchKernelEx(&cfg, k1_tc2_topk<MODE, KL, EG>, a0, a1, b0, b1, A) == cudaSuccess;
 }
 
+// items: work items of the launch, or INT_MAX when only the device knows
+// them (gathered rows): then every resident pair is launched.
 template <int MODE>
-bool launch_mode_pair(const CUtensorMap& a, const CUtensorMap& b, const TcArgs& A, int eg, int items, int sm_count,
-                      cudaStream_t s) {
+bool launch_mode_pair(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& b0, const CUtensorMap& b1,
+                      const TcArgs& A, int eg, int items, int sm_count, cudaStream_t s) {
   if (A.K <= 48)
-    return eg == 2 ? launch_kl_pair<MODE, 48, 2>(a, b, A, items, sm_count, s)
-                   : launch_kl_pair<MODE, 48, 1>(a, b, A, items, sm_count, s);
-  return eg == 2 ? launch_kl_pair<MODE, KLIST, 2>(a, b, A, items, sm_count, s)
-                 : launch_kl_pair<MODE, KLIST, 1>(a, b, A, items, sm_count, s);
+    return eg == 2 ? launch_kl_pair<MODE, 48, 2>(a0, a1, b0, b1, A, items, sm_count, s)
+                   : launch_kl_pair<MODE, 48, 1>(a0, a1, b0, b1, A, items, sm_count, s);
+  return eg == 2 ? launch_kl_pair<MODE, KLIST, 2>(a0, a1, b0, b1, A, items, sm_count, s)
+                 : launch_kl_pair<MODE, KLIST, 1>(a0, a1, b0, b1, A, items, sm_count, s);
 }
 
 // The per-row list lives in registers, so its length is a compile-time choice.
@@ -926,8 +929,8 @@ int launch_sim_tc_topk(const Shape& sh, const void* xlow, bool fp8, const float*
   }
   const int items = A.row_blocks * A.chunks;
   if (pairs) {
-    const bool ok = fp8 ? launch_mode_pair<MODE_FP8>(map, map, A, eg, items, sm_count, s)
-                        : launch_mode_pair<MODE_BF16>(map, map, A, eg, items, sm_count, s);
+    const bool ok = fp8 ? launch_mode_pair<MODE_FP8>(map, map, map, map, A, eg, items, sm_count, s)
+                        : launch_mode_pair<MODE_BF16>(map, map, map, map, A, eg, items, sm_count, s);
     return ok ? 1 : -1;
   }
   const int grid = items < sm_count ? items : sm_count;
@@ -1000,6 +1003,9 @@ int launch_sim_tc_split_topk(const Shape& sh, int P3, const __nv_bfloat16* ahi, 
   A.part_i = part_i;
   A.status = status;
   A.stall = stall_hook();
+  // CTA pairs when the rows come in whole 256-row blocks of the padded buffers.
+  if (tc_pairs() && sm_count >= 2 && sh.np % (2 * TBM) == 0)
+    return launch_mode_pair<MODE_SPLIT>(a0, a1, b0, b1, A, eg, INT_MAX, sm_count, s) ? 1 : -1;
   launch_mode<MODE_SPLIT>(a0, a1, b0, b1, A, eg, sm_count, s);
   return 1;
 }
@@ -1083,6 +1089,8 @@ int launch_sim_tc_gather_topk(const Shape& sh, int P, const __nv_bfloat16* ahi, 
   A.part_i = part_i;
   A.status = status;
   A.stall = stall_hook();
+  if (tc_pairs() && sm_count >= 2 && sh.np % (2 * TBM) == 0)
+    return launch_mode_pair<MODE_GATHER>(a0, a0, b0, b0, A, eg, INT_MAX, sm_count, s) ? 1 : -1;
   launch_mode<MODE_GATHER>(a0, a0, b0, b0, A, eg, sm_count, s);
   return 1;
 }
