@@ -248,7 +248,7 @@ def _config(args, w):
 
 # DRAM bytes (read + write) of one similarity launch, from `ncu --set full` captures
 # of the current kernel (profiles/); None where no capture of it exists.
-SIM_TRAFFIC_BYTES = {("bf16", "market"): 340.7e6}  # profiles/k1_tc2_topk_bf16_market_23k_d2048.md
+SIM_TRAFFIC_BYTES = {("bf16", "market"): 314.9e6}  # profiles/k1_tc2_topk_bf16_market_23k_d2048.md
 # DRAM bytes of the refinement's first pass, same source
 # (profiles/k2_refine_cta_bf16_market_23k_d2048.md).
 REFINE_DRAM_BYTES = {("bf16", "market"): 1.725e9}
