@@ -537,7 +537,9 @@ k6_rank_dense(const float* __restrict__ S, int64_t nq, int64_t ng, int64_t topk,
   }
 }
 
-// and radix paths on small inputs; all paths give identical lists.
+// Test hook: RERANK_TEST_RANK_CAPS = "sort_cap,bucket_cap" lowers the limits,
+// so that small inputs take the global-key and radix paths; all paths give
+// identical lists.
 void rank_caps(int* sort_cap, int* bucket_cap) {
   *sort_cap = SORT_CAP;
   *bucket_cap = BUCKET_CAP;
