@@ -416,22 +416,6 @@ k2_refine(RowIo io, int64_t n, const float* __restrict__ part_s, const int32_t* 
   }
 }
 
-// Rank of each rescored candidate among [0, n): w.ord[rank] = candidate (one
-// warp).  As in refine_warp: valid positions first, so a malformed list can
-// never send a later read out of range.
-__device__ void rank_cands(WarpSmem& w, int n, int lane) {
-  for (int c = lane; c < n; c += kWarp) w.ord[c] = c;
-  __syncwarp();
-  for (int c = lane; c < n; c += kWarp) {
-    const float sc = w.s[c];
-    const int ic = w.idx[c];
-    int r = 0;
-    for (int e = 0; e < n; ++e) r += ranks_before(w.s[e], w.idx[e], sc, ic) ? 1 : 0;
-    w.ord[r] = c;
-  }
-  __syncwarp();
-}
-
 // Merge of the P sorted candidate lists of a row by all threads of a CTA
 // (the lists staged in shared memory, P * K <= MERGE_CAP): an entry's place in
 // the merged order is its position in its own list plus, for every other
