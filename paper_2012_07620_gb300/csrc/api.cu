@@ -156,6 +156,7 @@ size_t carve(Carver& c, const Shape& sh, Buffers& b, int sm_count, int precision
   }
   b.ub = c.take<int32_t>(size_t(n));
   b.big_rows = c.take<int32_t>(size_t(n));
+  b.prop_spill = c.take<int32_t>(size_t(n));
   b.big_count = c.take<int32_t>(4);
   b.hash_keys_vals = c.take<float>(size_t(sm_count) * (size_t(n) + size_t((n + 31) / 32)));
   b.rnorm = c.take<float>(size_t(n));

@@ -109,7 +109,8 @@ struct Buffers {
   int32_t* col[3] = {nullptr, nullptr, nullptr};
   float* val[3] = {nullptr, nullptr, nullptr};
   int32_t* ub = nullptr;         // n
-  int32_t* big_rows = nullptr;   // n
+  int32_t* big_rows = nullptr;    // n: rows the first propagation pass hands on
+  int32_t* prop_spill = nullptr;  // n: per listed row, 1 when its 2,048-slot table overflowed
   int32_t* big_count = nullptr;
   float* hash_keys_vals = nullptr; // global hash tables of the big-row path
   float* rnorm = nullptr;        // n, 1/||h_i^(L)||

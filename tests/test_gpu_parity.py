@@ -259,6 +259,43 @@ def test_rank_sort_paths_agree():
     assert len(set(digests)) == 1, digests
 
 
+def test_propagation_paths_agree():
+    """A layer row goes through a 512-slot warp table; rows that overflow it
+    take a second pass with 2,048-slot tables when there are at least 4 per
+    SM, else (and beyond 1,536 distinct columns) one CTA per row with a dense
+    accumulator.  With noisy features (norm 1.2 around the centres), k1 = 40
+    and k2 = 16, 2,839 of the 3,000 second-layer rows here have more than 384
+    columns and 11 more than 1,536.  A test hook sends every overflowing row to the
+    second pass or every one to the CTA path: the ranked lists and distances
+    are the same bit for bit (each column is summed in message order and the
+    norm is an exact fixed-point sum on every path), and match the oracle."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch, sys, hashlib; sys.path.insert(0, '.'); sys.path.insert(0, 'tests');"
+        "import parity; from oracle import rerank_oracle as o;"
+        "from paper_2012_07620_gb300 import rerank, synthetic;"
+        "w = synthetic.make_workload(synthetic.WorkloadSpec('spill', 300, 2700, 64, 100, 1.2, 0, None, seed=17));"
+        "R = rerank.Reranker(); i, d = R.run(torch.from_numpy(w.xq).cuda(), torch.from_numpy(w.xg).cuda(), 40, 16, 2);"
+        "torch.cuda.synchronize(); i, d = i.cpu().numpy(), d.cpu().numpy();"
+        "ref = o.rerank(w.xq, w.xg, 40, 16, 2, mode='sparse');"
+        "nz = np.diff(ref.h[-1].tocsr().indptr); assert (nz > 384).sum() > 100, (nz > 384).sum();"
+        "parity.assert_ranked_equal(i, d, ref.s, ref.idx);"
+        "print('digest', hashlib.sha256(i.tobytes() + d.tobytes()).hexdigest())"
+    )
+    digests = []
+    for second_min in (None, "0", "1000000000"):
+        env = dict(os.environ)
+        env.pop("RERANK_TEST_PROP_SECOND_MIN", None)
+        if second_min:
+            env["RERANK_TEST_PROP_SECOND_MIN"] = second_min
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and "digest" in r.stdout, (second_min, r.stderr[-2000:])
+        digests.append(r.stdout.split("digest")[-1].strip())
+    assert len(set(digests)) == 1, digests
+
+
 @pytest.mark.parametrize("precision", ["fp32", "bf16"])
 def test_no_rescore_margin_sends_rows_to_the_exact_scan(precision):
     """With rescore_m = 0 the first pass keeps exactly k1 candidates, so no
