@@ -251,7 +251,7 @@ def _config(args, w):
 SIM_TRAFFIC_BYTES = {("bf16", "market"): 314.9e6}  # profiles/k1_tc2_topk_bf16_market_23k_d2048.md
 # DRAM bytes of the refinement's first pass, same source
 # (profiles/k2_refine_cta_bf16_market_23k_d2048.md).
-REFINE_DRAM_BYTES = {}
+REFINE_DRAM_BYTES = {("bf16", "market"): 1.682e9}
 
 
 def _stage_rooflines(precision, stages, nq, ng, d, k1, k2, rescore_m, h_nnz, layers, workload):
