@@ -310,10 +310,10 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
              const int32_t* __restrict__ nbr_n, int k2p1, const int32_t* __restrict__ ub,
              const int64_t* __restrict__ dstart, int32_t* __restrict__ dlen, int32_t* __restrict__ dcol,
              float* __restrict__ dval, int64_t n, int64_t cap, int32_t* __restrict__ big_rows,
-             int32_t* __restrict__ big_count, long long* __restrict__ status, bool agg_max, LayerReuse reuse,
-             unsigned long long* __restrict__ nnz_out) {
+             int32_t* __restrict__ big_count, int32_t* __restrict__ next_row, long long* __restrict__ status,
+             bool agg_max, LayerReuse reuse, unsigned long long* __restrict__ nnz_out) {
   extern __shared__ int smem_i[];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* keys = smem_i + wib * WSLOTS * 2;
   float* vals = reinterpret_cast<float*>(smem_i + wib * WSLOTS * 2 + WSLOTS);
   if (!capacity_ok(dstart, n, cap, status)) return;
@@ -323,7 +323,14 @@ k4_spmm_warp(const int64_t* __restrict__ sstart, const int32_t* __restrict__ sle
   }
   __syncwarp();
   unsigned long long nnz = 0;  // entries this warp wrote (lane 0)
-  for (int64_t i = int64_t(blockIdx.x) * nw + wib; i < n; i += int64_t(gridDim.x) * nw) {
+  // Rows are taken one at a time from a counter: their cost varies with the
+  // length of their message rows, and a static split left the busiest SM
+  // with twice the average work (market, second layer).
+  for (;;) {
+    int64_t i = 0;
+    if (lane == 0) i = atomicAdd(next_row, 1);
+    i = __shfl_sync(kFull, i, 0);
+    if (i >= n) break;
     if (reuse.changed && !reuse.changed[i]) {
       // inputs unchanged: the known row, in its own column order
       const int64_t g = i - reuse.shift, a = reuse.rstart[g], o = dstart[i];
@@ -543,7 +550,7 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
   const int64_t n = sh.n;
   const int k2p1 = sh.k2 + 1;
   const int T = 256;
-  cudaMemsetAsync(b.big_count, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(b.big_count, 0, 2 * sizeof(int32_t), s);  // [0]: rows handed on, [1]: next row of the first pass
   const LayerReuse ru = reuse ? *reuse : LayerReuse{};
   k4_ub<<<unsigned((n + T - 1) / T), T, 0, s>>>(b.nbr, b.nbr_n, k2p1, b.len[src], n, b.ub, b.big_rows, b.big_count,
                                                  status, ru);
@@ -556,8 +563,9 @@ int launch_propagate(const Shape& sh, const Buffers& b, int src, int dst, int ag
   const unsigned blocks = unsigned(tmin<int64_t>(blocks_needed, int64_t(sm_count) * (per_sm > 0 ? per_sm : 1)));
   k4_spmm_warp<<<blocks, warps * kWarp, smem, s>>>(b.start[src], b.len[src], b.col[src], b.val[src], b.nbr, b.nbr_w,
                                                    b.nbr_n, k2p1, b.ub, b.start[dst], b.len[dst], b.col[dst],
-                                                   b.val[dst], n, sh.cap_h, b.big_rows, b.big_count, status,
-                                                   aggregator == RERANK_AGG_MAX, ru, nnz_out);
+                                                   b.val[dst], n, sh.cap_h, b.big_rows, b.big_count,
+                                                   b.big_count + 1, status, aggregator == RERANK_AGG_MAX, ru,
+                                                   nnz_out);
   // The rows the first pass listed: 2,048-slot tables when there are at least
   // 4 per SM (market_hard: 21,906 rows, propagation 2.20 -> 1.13 ms), else the
   // CTA path (market: 549 rows, faster there).
