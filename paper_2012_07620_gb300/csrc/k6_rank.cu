@@ -495,43 +495,139 @@ size_t rank_smem_fixed(int64_t ng) {
   return sizeof(uint32_t) * (RW * 256 + 64 + ((nwords + 3) & ~int64_t(3))) + sizeof(uint64_t) * SORT_CAP;
 }
 
-// Test hook: RERANK_TEST_RANK_CAPS="s,b" lowers the bucket sort's limits (s
-// keys in shared memory, buckets of b keys) so that tests reach the global-key
 // Dense final features (h^(0) = x_i): one query per CTA ranks all its gallery
 // scores S[q][0 .. ng), which may be negative.  A score's 32-bit sort key is
 // its IEEE bits mapped to an unsigned order (negatives reversed, -0 taken as
-// +0), inverted so that ascending keys are descending scores; the stable LSD
-// radix sort over the keys in gallery order keeps equal scores in ascending
-// gallery index.  The four key / index arrays live in the CTA's global
-// scratch (4 ng words).
+// +0), inverted so that ascending keys are descending scores; with the
+// gallery index below it (64-bit key) the keys are distinct and their
+// ascending order is the ranking (equal scores in ascending gallery index).
+// Buckets in two levels, so that they hold a few keys each whatever the
+// distribution: level one splits the key space into 8,192 bins of 2^19 keys
+// (a sixteenth of an octave of the score), and a bin of c keys is cut into
+// ceil(c / 4) equal key ranges, the buckets (in key order).  Keys are
+// scattered to their bucket's range in the CTA's global scratch (L2-resident)
+// and a key's place in its bucket is the number of smaller keys there.  A
+// query with more than NBD2 buckets or a bucket of more than bucket_cap keys
+// (e.g. many equal scores) takes the stable LSD radix sort in the same
+// scratch instead (4 ng words).
+constexpr int NBD1 = 8192;        // level-one bins (2^19 keys each)
+constexpr int NBD2 = 16384;       // buckets
+constexpr int DBUCKET_CAP = 256;  // largest bucket the counting step takes
+constexpr size_t DENSE_SMEM = sizeof(uint32_t) * (2 * NBD1 + NBD2);  // bin counts, bin bases, bucket counters
+
+__device__ __forceinline__ uint32_t dense_key(float sc) {
+  const uint32_t u = sc == 0.0f ? 0u : __float_as_uint(sc);
+  const uint32_t up = (u & 0x80000000u) ? ~u : (u | 0x80000000u);  // ascending with the score
+  return ~up;
+}
+
 __global__ void __launch_bounds__(RT, 1)
 k6_rank_dense(const float* __restrict__ S, int64_t nq, int64_t ng, int64_t topk, int32_t* __restrict__ out_idx,
-              float* __restrict__ out_dist, uint32_t* __restrict__ gscratch, const long long* __restrict__ status) {
-  __shared__ uint32_t hist[RW * 256];
+              float* __restrict__ out_dist, uint32_t* __restrict__ gscratch, int bucket_cap,
+              const long long* __restrict__ status) {
+  extern __shared__ uint32_t dsm[];
+  uint32_t* bcnt = dsm;              // NBD1: keys per bin
+  uint32_t* bbase = dsm + NBD1;      // NBD1: first bucket of each bin
+  uint32_t* hist = dsm + 2 * NBD1;   // NBD2 bucket counters (also the radix histograms)
   __shared__ int tmp[32];
+  __shared__ uint32_t wmax[RW];
   __shared__ int skip;
   if (status[kStErr] & kErrOverflow) return;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   uint32_t* base = gscratch + size_t(blockIdx.x) * size_t(scratch_words(ng));
+  uint64_t* kb = reinterpret_cast<uint64_t*>(base);  // ng keys in bucket order (2 ng words)
+  auto bucket = [&](uint32_t k) {
+    const int bin = int(k >> 19);
+    return int(bbase[bin] + ((uint64_t(k & 0x7ffffu) * ((bcnt[bin] + 3u) >> 2)) >> 19));
+  };
   for (int64_t q = blockIdx.x; q < nq; q += gridDim.x) {
-    uint32_t* keys = base;
-    uint32_t* vals = base + ng;
-    uint32_t* tkeys = base + 2 * ng;
-    uint32_t* tvals = base + 3 * ng;
     const float* sq = S + q * ng;
-    for (int64_t g = t; g < ng; g += RT) {
-      const float sc = sq[g];
-      const uint32_t u = sc == 0.0f ? 0u : __float_as_uint(sc);
-      const uint32_t up = (u & 0x80000000u) ? ~u : (u | 0x80000000u);  // ascending with the score
-      keys[g] = ~up;
-      vals[g] = uint32_t(g);
-    }
+    for (int e = t; e < NBD1; e += RT) bcnt[e] = 0u;
+    for (int e = t; e < NBD2; e += RT) hist[e] = 0u;
     __syncthreads();
-    block_radix_sort(keys, vals, tkeys, tvals, int(ng), hist, tmp, &skip);
-    for (int64_t p = t; p < topk; p += RT) {
-      const uint32_t g = vals[p];
-      out_idx[q * topk + p] = int32_t(g);
-      out_dist[q * topk + p] = 1.0f - sq[g];
+    for (int64_t g = t; g < ng; g += RT) atomicAdd(&bcnt[dense_key(sq[g]) >> 19], 1u);
+    __syncthreads();
+    {
+      // bbase = exclusive scan of ceil(bcnt / 4), eight bins per thread.
+      uint32_t c[NBD1 / RT];
+      int part = 0;
+#pragma unroll
+      for (int k = 0; k < NBD1 / RT; ++k) {
+        c[k] = (bcnt[t * (NBD1 / RT) + k] + 3u) >> 2;
+        part += int(c[k]);
+      }
+      int start;
+      const int nbk = block_exscan(part, tmp, start);
+#pragma unroll
+      for (int k = 0; k < NBD1 / RT; ++k) {
+        bbase[t * (NBD1 / RT) + k] = uint32_t(start);
+        start += int(c[k]);
+      }
+      if (t == 0) skip = nbk > NBD2 ? 1 : 0;
+      __syncthreads();
+    }
+    bool small = skip == 0;
+    if (small) {
+      for (int64_t g = t; g < ng; g += RT) atomicAdd(&hist[bucket(dense_key(sq[g]))], 1u);
+      __syncthreads();
+      uint32_t c[NBD2 / RT];
+      int part = 0, big = 0;
+#pragma unroll
+      for (int k = 0; k < NBD2 / RT; ++k) {
+        c[k] = hist[t * (NBD2 / RT) + k];
+        part += int(c[k]);
+        big = max(big, int(c[k]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
+      if (lane == 0) wmax[w] = uint32_t(big);
+      int start;
+      block_exscan(part, tmp, start);  // its barriers also publish wmax
+      for (int k = 0; k < RW; ++k) small = small && int(wmax[k]) <= bucket_cap;
+      if (small) {
+#pragma unroll
+        for (int k = 0; k < NBD2 / RT; ++k) {
+          hist[t * (NBD2 / RT) + k] = uint32_t(start);
+          start += int(c[k]);
+        }
+        __syncthreads();
+        for (int64_t g = t; g < ng; g += RT) {
+          const uint32_t k = dense_key(sq[g]);
+          const uint32_t pos = atomicAdd(&hist[bucket(k)], 1u);
+          kb[pos] = (uint64_t(k) << 32) | uint64_t(g);
+        }
+        __syncthreads();  // hist[b] is now the end of bucket b
+        for (int64_t p = t; p < ng; p += RT) {
+          const uint64_t key = kb[p];
+          const int bk = bucket(uint32_t(key >> 32));
+          const int b0 = bk ? int(hist[bk - 1]) : 0, b1 = int(hist[bk]);
+          int r = 0;
+          for (int j = b0; j < b1; ++j) r += kb[j] < key;
+          const int64_t pos = b0 + r;
+          if (pos < topk) {
+            const uint32_t g = uint32_t(key);
+            out_idx[q * topk + pos] = int32_t(g);
+            out_dist[q * topk + pos] = 1.0f - sq[g];
+          }
+        }
+      }
+    }
+    if (!small) {
+      uint32_t* keys = base;
+      uint32_t* vals = base + ng;
+      uint32_t* tkeys = base + 2 * ng;
+      uint32_t* tvals = base + 3 * ng;
+      for (int64_t g = t; g < ng; g += RT) {
+        keys[g] = dense_key(sq[g]);
+        vals[g] = uint32_t(g);
+      }
+      __syncthreads();
+      block_radix_sort(keys, vals, tkeys, tvals, int(ng), hist, tmp, &skip);
+      for (int64_t p = t; p < topk; p += RT) {
+        const uint32_t g = vals[p];
+        out_idx[q * topk + p] = int32_t(g);
+        out_dist[q * topk + p] = 1.0f - sq[g];
+      }
     }
     __syncthreads();
   }
@@ -626,7 +722,11 @@ int rank_threads() { return RT; }
 int launch_rank_dense(const Shape& sh, const float* S, int32_t* out_idx, float* out_dist, uint32_t* scratch,
                       long long* status, cudaStream_t s) {
   const unsigned grid = unsigned(sh.nq < sh.rank_ctas ? sh.nq : sh.rank_ctas);
-  k6_rank_dense<<<grid, RT, 0, s>>>(S, sh.nq, sh.ng, sh.topk, out_idx, out_dist, scratch, status);
+  int sort_cap = 0, bucket_cap = 0;
+  rank_caps(&sort_cap, &bucket_cap);  // a test lowering the bucket cap sends queries to the radix sort
+  cudaFuncSetAttribute(k6_rank_dense, cudaFuncAttributeMaxDynamicSharedMemorySize, int(DENSE_SMEM));
+  k6_rank_dense<<<grid, RT, DENSE_SMEM, s>>>(S, sh.nq, sh.ng, sh.topk, out_idx, out_dist, scratch,
+                                             bucket_cap < DBUCKET_CAP ? bucket_cap : DBUCKET_CAP, status);
   return 1;
 }
 

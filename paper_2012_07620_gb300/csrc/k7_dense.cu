@@ -12,7 +12,7 @@
 // sum of squares, the 32 partials added in FP64).
 //
 // Scores: s(q, g) = <h_q, h_g> / (||h_q|| ||h_g||) for every query row q and
-// gallery row g, 64 x 64 output tiles per CTA, 4 x 4 per thread.  Each
+// gallery row g, 128 x 128 output tiles per CTA, 8 x 8 per thread.  Each
 // 32-deep k-chunk is an FP32 FMA chain; the chunks are added in float-float
 // (a TwoSum per chunk), so a score is as accurate as a chain of 32 products
 // (about 1e-7 for unit rows) whatever d is; the norms are applied in FP64.
@@ -22,9 +22,7 @@
 namespace rr {
 namespace {
 
-constexpr int DT = 64;   // output tile (queries x gallery rows)
-constexpr int DK = 32;   // k-chunk
-constexpr int DTHREADS = 256;
+constexpr int DK = 32;   // k-chunk of the scores
 
 // out_i = normalise(sum_m c_m h_{j_m})  (sum / mean), or
 // normalise(max_m (c_m h_{j_m}) + h_i)   (max; the residual entry has c < 0).
@@ -122,69 +120,110 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float p) {
   lo += err;
 }
 
-__global__ void __launch_bounds__(DTHREADS)
+// Scores by 128 x 128 output tiles, 256 threads of 8 x 8 outputs each (rows
+// 4 ty + a and 64 + 4 ty + a, columns 4 tx + b and 64 + 4 tx + b).  Each
+// 32-deep k-chunk is an FP32 FMA chain per output in k order and is added to
+// the output's (hi, lo) pair by TwoSum, so a score does not depend on the
+// tile shape or on which thread computes it; 8 x 8 outputs per thread keep
+// the shared-memory reads at a quarter of the FMAs' operands.  The chunk sums p and
+// hi live in registers, lo in shared memory (read and written once per
+// chunk).  The operand chunks are stored k-major (lane = row when loading, so
+// the transposing stores are free of bank conflicts); the next chunk's global
+// loads are issued before the current chunk is used.
+constexpr int ST = 128;                 // output tile
+constexpr int STHREADS = 256;
+constexpr size_t SSMEM = size_t(2) * DK * ST * 4 + size_t(64) * STHREADS * 4;  // As, Bs, lo
+
+__global__ void __launch_bounds__(STHREADS, 1)
 k7_dense_scores(const float* __restrict__ h, int64_t nq, int64_t ng, int dp, const double* __restrict__ inv,
                 float* __restrict__ S) {
-  __shared__ float4 As[DK][DT / 4];  // k-major: As[k][r / 4] holds rows r .. r + 3
-  __shared__ float4 Bs[DK][DT / 4];
-  const int t = threadIdx.x;
-  const int tx = t & 15, ty = t >> 4;  // 16 x 16 threads, 4 x 4 outputs each
-  const int64_t q0 = int64_t(blockIdx.y) * DT, g0 = int64_t(blockIdx.x) * DT;
-  float hi[4][4], lo[4][4];
+  extern __shared__ float4 dyn4[];
+  float* As = reinterpret_cast<float*>(dyn4);  // [DK][ST]
+  float* Bs = As + DK * ST;                    // [DK][ST]
+  float* lo = Bs + DK * ST;                    // [64][STHREADS]
+  const int t = threadIdx.x, lane = t & 31, wq = t >> 5;
+  const int tx = t & 15, ty = t >> 4;
+  const int64_t q0 = int64_t(blockIdx.y) * ST, g0 = int64_t(blockIdx.x) * ST;
+  float hi[64], p[64];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int j = 0; j < 64; ++j) {
+    hi[j] = 0.f;
+    lo[j * STHREADS + t] = 0.f;
+  }
+  // Loader: warp wq moves k-group wq (4 consecutive k of the chunk) of rows
+  // lane + 32 s, s = 0..3, for both operands.
+  const float4* arow[4];
+  const float4* brow[4];
+  bool aok[4], bok[4];
 #pragma unroll
-    for (int b = 0; b < 4; ++b) hi[a][b] = lo[a][b] = 0.f;
-  // Loader: thread t moves rows r = t / 4 (0..63) and columns (t % 4) * 8 .. + 7 of the chunk.
-  const int lr = t >> 2, lc = (t & 3) * 8;
-  const bool qa = q0 + lr < nq, ga = g0 + lr < ng;
-  const float* qa_row = h + size_t(qa ? q0 + lr : 0) * dp;
-  const float* ga_row = h + size_t(ga ? nq + g0 + lr : 0) * dp;
+  for (int sl = 0; sl < 4; ++sl) {
+    const int64_t qa = q0 + lane + 32 * sl, ga = g0 + lane + 32 * sl;
+    aok[sl] = qa < nq;
+    bok[sl] = ga < ng;
+    arow[sl] = reinterpret_cast<const float4*>(h + size_t(aok[sl] ? qa : 0) * dp) + wq;
+    brow[sl] = reinterpret_cast<const float4*>(h + size_t(bok[sl] ? nq + ga : 0) * dp) + wq;
+  }
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 va[4], vb[4];
+#pragma unroll
+  for (int sl = 0; sl < 4; ++sl) {
+    va[sl] = aok[sl] ? __ldg(arow[sl]) : zero;
+    vb[sl] = bok[sl] ? __ldg(brow[sl]) : zero;
+  }
   for (int k0 = 0; k0 < dp; k0 += DK) {
-    float va[8], vb[8];
-    const float4 a0 = qa ? __ldg(reinterpret_cast<const float4*>(qa_row + k0 + lc)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 a1 =
-        qa ? __ldg(reinterpret_cast<const float4*>(qa_row + k0 + lc + 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 b0 = ga ? __ldg(reinterpret_cast<const float4*>(ga_row + k0 + lc)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 b1 =
-        ga ? __ldg(reinterpret_cast<const float4*>(ga_row + k0 + lc + 4)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    va[0] = a0.x; va[1] = a0.y; va[2] = a0.z; va[3] = a0.w; va[4] = a1.x; va[5] = a1.y; va[6] = a1.z; va[7] = a1.w;
-    vb[0] = b0.x; vb[1] = b0.y; vb[2] = b0.z; vb[3] = b0.w; vb[4] = b1.x; vb[5] = b1.y; vb[6] = b1.z; vb[7] = b1.w;
-    __syncthreads();
+    __syncthreads();  // the previous chunk is consumed
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      reinterpret_cast<float*>(&As[lc + u][0])[lr] = va[u];
-      reinterpret_cast<float*>(&Bs[lc + u][0])[lr] = vb[u];
+    for (int sl = 0; sl < 4; ++sl) {
+      const int r = lane + 32 * sl, kk = 4 * wq;
+      As[(kk + 0) * ST + r] = va[sl].x;
+      As[(kk + 1) * ST + r] = va[sl].y;
+      As[(kk + 2) * ST + r] = va[sl].z;
+      As[(kk + 3) * ST + r] = va[sl].w;
+      Bs[(kk + 0) * ST + r] = vb[sl].x;
+      Bs[(kk + 1) * ST + r] = vb[sl].y;
+      Bs[(kk + 2) * ST + r] = vb[sl].z;
+      Bs[(kk + 3) * ST + r] = vb[sl].w;
     }
     __syncthreads();
-    float p[4][4];
+    if (k0 + DK < dp) {
+      const int step = (k0 + DK) / 4;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+      for (int sl = 0; sl < 4; ++sl) {
+        va[sl] = aok[sl] ? __ldg(arow[sl] + step) : zero;
+        vb[sl] = bok[sl] ? __ldg(brow[sl] + step) : zero;
+      }
+    }
 #pragma unroll
-      for (int b = 0; b < 4; ++b) p[a][b] = 0.f;
-#pragma unroll 8
+    for (int j = 0; j < 64; ++j) p[j] = 0.f;
+#pragma unroll 4
     for (int k = 0; k < DK; ++k) {
-      const float4 x = As[k][ty], y = Bs[k][tx];
-      const float xa[4] = {x.x, x.y, x.z, x.w}, yb[4] = {y.x, y.y, y.z, y.w};
+      const float4 x0 = reinterpret_cast<const float4*>(As + k * ST)[ty];
+      const float4 x1 = reinterpret_cast<const float4*>(As + k * ST)[16 + ty];
+      const float4 y0 = reinterpret_cast<const float4*>(Bs + k * ST)[tx];
+      const float4 y1 = reinterpret_cast<const float4*>(Bs + k * ST)[16 + tx];
+      const float xa[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+      const float yb[8] = {y0.x, y0.y, y0.z, y0.w, y1.x, y1.y, y1.z, y1.w};
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) p[a][b] = fmaf(xa[a], yb[b], p[a][b]);
+        for (int b = 0; b < 8; ++b) p[a * 8 + b] = fmaf(xa[a], yb[b], p[a * 8 + b]);
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) ff_add(hi[a][b], lo[a][b], p[a][b]);
+    for (int j = 0; j < 64; ++j) {
+      float l = lo[j * STHREADS + t];
+      ff_add(hi[j], l, p[j]);
+      lo[j * STHREADS + t] = l;
+    }
   }
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int64_t q = q0 + ty * 4 + a;
+  for (int a = 0; a < 8; ++a) {
+    const int64_t q = q0 + (a < 4 ? 4 * ty + a : 64 + 4 * ty + (a - 4));
     if (q >= nq) continue;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int64_t g = g0 + tx * 4 + b;
+    for (int b = 0; b < 8; ++b) {
+      const int64_t g = g0 + (b < 4 ? 4 * tx + b : 64 + 4 * tx + (b - 4));
       if (g >= ng) continue;
-      const double dot = double(hi[a][b]) + double(lo[a][b]);
+      const double dot = double(hi[a * 8 + b]) + double(lo[(a * 8 + b) * STHREADS + t]);
       S[q * ng + g] = float(dot * inv[q] * inv[nq + g]);
     }
   }
@@ -203,8 +242,9 @@ int launch_dense_layer(const Shape& sh, const float* hin, float* hout, const int
 int launch_dense_scores(const Shape& sh, const float* h, double* inv, float* S, cudaStream_t s) {
   const int T = 256;
   k7_dense_inv_norms<<<unsigned((sh.n * kWarp + T - 1) / T), T, 0, s>>>(h, sh.n, sh.dp, inv);
-  dim3 grid(unsigned((sh.ng + DT - 1) / DT), unsigned((sh.nq + DT - 1) / DT));
-  k7_dense_scores<<<grid, DTHREADS, 0, s>>>(h, sh.nq, sh.ng, sh.dp, inv, S);
+  dim3 grid(unsigned((sh.ng + ST - 1) / ST), unsigned((sh.nq + ST - 1) / ST));
+  cudaFuncSetAttribute(k7_dense_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SSMEM));
+  k7_dense_scores<<<grid, STHREADS, SSMEM, s>>>(h, sh.nq, sh.ng, sh.dp, inv, S);
   return 2;
 }
 

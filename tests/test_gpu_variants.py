@@ -100,6 +100,42 @@ def test_dense_features_match_oracle(lib, inst, aggregator, alpha, layers, preci
     assert stats["max_dist_err"] < 1e-5
 
 
+def test_dense_ranking_paths_agree():
+    """The dense ranking sorts each query's scores by one bucket pass (keys in
+    global scratch, a key's place = its bucket's start + the smaller keys in
+    it); a query with a crowded bucket takes a 4-pass radix sort instead.  A
+    test hook lowers the bucket cap to 1, so that every query takes the radix
+    sort: both give the same lists, bit for bit, including a group of equal
+    scores (copies of one gallery row), and match the oracle."""
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import numpy as np, torch, sys, hashlib; sys.path.insert(0, '.'); sys.path.insert(0, 'tests');"
+        "import parity; from oracle import rerank_oracle as o;"
+        "from paper_2012_07620_gb300 import rerank, synthetic;"
+        "w = synthetic.make_workload(synthetic.WorkloadSpec('dense_sort', 80, 2920, 64, 100, 0.6, 0, None, seed=23));"
+        "xg = w.xg.copy(); xg[200:206] = xg[11];"
+        "R = rerank.Reranker(feature='x'); tq, tg = torch.from_numpy(w.xq).cuda(), torch.from_numpy(xg).cuda();"
+        "i, d = R.run(tq, tg, 20, 5, 1); i2, d2 = R.run(tq, tg, 20, 5, 1, 100);"
+        "torch.cuda.synchronize(); i, d, i2, d2 = (a.cpu().numpy() for a in (i, d, i2, d2));"
+        "ref = o.rerank(w.xq, xg, 20, 5, 1, feature='x', mode='dense');"
+        "parity.assert_ranked_equal(i, d, ref.s, ref.idx); parity.assert_ranked_equal(i2, d2, ref.s, ref.idx, 100);"
+        "assert (i2 == i[:, :100]).all() and (d2 == d[:, :100]).all();"
+        "print('digest', hashlib.sha256(i.tobytes() + d.tobytes()).hexdigest())"
+    )
+    digests = []
+    for caps in (None, "8192,1"):
+        env = dict(os.environ)
+        env.pop("RERANK_TEST_RANK_CAPS", None)
+        if caps:
+            env["RERANK_TEST_RANK_CAPS"] = caps
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0 and "digest" in r.stdout, (caps, r.stderr[-2000:])
+        digests.append(r.stdout.split("digest")[-1].strip())
+    assert len(set(digests)) == 1, digests
+
+
 def test_dense_features_without_layers_give_the_initial_ranking(lib, inst):
     """x_i features with L = 0: the list of every query is the gallery sorted by
     cos(x_q, x_g), ties to the lower index (Table 1, first column = the
