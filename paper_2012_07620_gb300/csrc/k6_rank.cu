@@ -452,7 +452,8 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     }
     // The zero tail in gallery order.  Its distances are all 1: plain
     // block-wide stores, 16 bytes each once aligned.  Its indices: warp w
-    // writes the zeros of its words, four words per step.
+    // writes the zeros of its words (a warp scan of 32 words' zero counts,
+    // then one coalesced store per word).
     if (T > cnt) {
       float* dq = A.out_dist + q * T;
       const int64_t head = tmin<int64_t>((4 - int((reinterpret_cast<uintptr_t>(dq + cnt) >> 2) & 3)) & 3, T - cnt);
@@ -462,24 +463,36 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
       for (int64_t v = t; v < nv; v += RT) dv[v] = make_float4(1.f, 1.f, 1.f, 1.f);
       for (int64_t p = p0 + 4 * nv + t; p < T; p += RT) dq[p] = 1.0f;
       int32_t* iq = A.out_idx + q * T;
-      int64_t pos = cnt + zeros_before;
-      for (int wd0 = w0; wd0 < w1 && pos < T; wd0 += 4) {
-        uint32_t zb[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int wd = wd0 + u;
-          const int valid = wd < w1 ? int(tmin<int64_t>(32, ng - int64_t(wd) * 32)) : 0;
+      // The warp's words 32 at a time: lane l takes word c0 + l, its zeros and
+      // their count; a warp scan of the counts gives every word's first place,
+      // then the warp writes the words' indices one word at a time.
+      int64_t run = int64_t(cnt) + zeros_before;
+      for (int c0 = w0; c0 < w1 && run < T; c0 += kWarp) {
+        const int nw = min(kWarp, w1 - c0);
+        uint32_t zl = 0u;
+        if (lane < nw) {
+          const int wd = c0 + lane;
+          const int valid = int(tmin<int64_t>(32, ng - int64_t(wd) * 32));
           const uint32_t vm = valid == 32 ? kFull : ((1u << valid) - 1u);
-          zb[u] = wd < w1 ? (~bits[wd] & vm) : 0u;
+          zl = ~bits[wd] & vm;
         }
+        const int cz = __popc(zl);
+        int incl = cz;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if ((zb[u] >> lane) & 1u) {
-            const int64_t p = pos + __popc(zb[u] & lt);
-            if (p < T) iq[p] = int32_t(int64_t(wd0 + u) * 32 + lane);
-          }
-          pos += __popc(zb[u]);
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
         }
+        const int64_t wbase = run + (incl - cz);
+        for (int j = 0; j < nw; ++j) {
+          const uint32_t zj = __shfl_sync(kFull, zl, j);
+          const int64_t bj = __shfl_sync(kFull, wbase, j);
+          if ((zj >> lane) & 1u) {
+            const int64_t p = bj + __popc(zj & lt);
+            if (p < T) iq[p] = int32_t(int64_t(c0 + j) * 32 + lane);
+          }
+        }
+        run += __shfl_sync(kFull, incl, 31);
       }
     }
     __syncthreads();
