@@ -16,7 +16,8 @@
 // the next 7 bits (4,096 log-spaced buckets, monotone in the score), keys are
 // scattered to their bucket's range, and each key's place inside its bucket is
 // the number of smaller keys there.  The keys live in shared memory up to
-// 8,192 of them, beyond that in the CTA's global scratch.  Queries with a
+// 8,192 of them, beyond that in the CTA's global scratch, where full lists cut
+// each bucket into ceil(count / 4) equal value ranges first.  Queries with a
 // bucket too crowded for the counting step (massive ties) use a stable LSD
 // radix sort in global memory (four 8-bit passes, per-warp digit histograms,
 // __match_any_sync ranks).  The zero tail follows in ascending gallery index.
@@ -332,122 +333,230 @@ __global__ void __launch_bounds__(RT, 1) k6_rank(RankArgs A) {
     // Keys of the bucket sort in shared memory up to sort_cap of them, else in
     // this CTA's global scratch (L1/L2-resident); the radix sort only when a
     // bucket is too crowded for the counting step.
-    const bool keys_smem = cnt <= A.sort_cap;
-    uint64_t* const kbx = keys_smem ? kb : kbg;
-    uint64_t* const ksx = keys_smem ? ks : ksg;
-    bool small = true;
-    {
-      // Bucket starts: exclusive scan of the histogram, four buckets per thread;
-      // the largest bucket up to bstar decides whether the counting step may run.
-      const bool whole = cut == cnt;  // every non-zero is returned: bstar is the last bucket
+    // Full lists whose keys go to global scratch (dense final features: every
+    // gallery score non-zero, about 20 keys per log bucket on average): each
+    // log bucket of c keys is cut into ceil(c / 4) equal value ranges, the
+    // sub-buckets, in the same order, so that the in-bucket counting reads a
+    // few keys per key.  Sub-bucket bases and counters live in the bucket-key
+    // space of shared memory (unused when the keys are in global scratch).
+    // When the sub-buckets do not fit, or one is still crowded, the query
+    // takes the log buckets below; the lists are the same either way.
+    bool done = false;
+    if (cnt > A.sort_cap && T >= cnt) {
+      uint32_t* sbase = reinterpret_cast<uint32_t*>(kb);  // NB: first sub-bucket of each log bucket
+      uint32_t* h2 = sbase + NB;                           // sub-bucket counters, then their ends
+      const int H2CAP = 2 * SORT_CAP - NB;
       uint32_t c[NB / RT];
-      int part = 0, big = 0;
+      int part = 0;
 #pragma unroll
       for (int k = 0; k < NB / RT; ++k) {
-        c[k] = hist[t * (NB / RT) + k];
+        c[k] = (hist[t * (NB / RT) + k] + 3u) >> 2;
         part += int(c[k]);
-        big = max(big, int(c[k]));
-      }
-      if (whole) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
-        if (lane == 0 && big > 0) atomicMax(&misc[1], big);
       }
       int base;
-      block_exscan(part, tmp, base);  // its barriers also publish misc[1]
+      const int nb2 = block_exscan(part, tmp, base);
+      if (nb2 <= H2CAP) {
 #pragma unroll
-      for (int k = 0; k < NB / RT; ++k) {
-        hist[t * (NB / RT) + k] = uint32_t(base);
-        if (!whole && base <= cut - 1 && cut - 1 < base + int(c[k])) misc[2] = t * (NB / RT) + k;
-        base += int(c[k]);
-      }
-      __syncthreads();
-      if (whole) {
-        bstar = cnt > 0 ? NB - 1 : -1;
-      } else {
-        bstar = misc[2];
-        big = 0;
-#pragma unroll
-        for (int k = 0; k < NB / RT; ++k)
-          if (t * (NB / RT) + k <= bstar) big = max(big, int(c[k]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
-        if (lane == 0 && big > 0) atomicMax(&misc[1], big);
+        for (int k = 0; k < NB / RT; ++k) {
+          sbase[t * (NB / RT) + k] = uint32_t(base);
+          base += int(c[k]);
+        }
+        for (int e = t; e < nb2; e += RT) h2[e] = 0u;
+        if (t == 0) misc[3] = 0;
         __syncthreads();
-      }
-      small = misc[1] <= A.bucket_cap;
-    }
-    if (small) {
-      // Scatter the non-zeros of buckets 0 .. bstar to their bucket's range
-      // (any order inside it); afterwards hist[b] is the end of bucket b.
-      for (int wd = w0; wd < w1; wd += 4) {
-        uint32_t bal[4], x[4];
+        // Sub-bucket of a non-zero x: its place inside its log bucket (the
+        // bits below the leading 8), scaled onto the bucket's ceil(c / 4)
+        // ranges, higher x first.
+        auto sub_bucket = [&](uint32_t x) {
+          const int bk = score_bucket(x);
+          const int sh = max(0, 24 - __clz(x));  // bits below the leading one and the 7 after it
+          const uint32_t r = x & ((1u << sh) - 1u);
+          const uint32_t ns = (hist[bk] + 3u) >> 2;
+          const uint32_t sub = uint32_t((uint64_t(r) * ns) >> sh);
+          return int(sbase[bk] + (ns - 1u - sub));
+        };
+        for (int wd = w0; wd < w1; wd += 4) {
+          uint32_t bal[4], x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
-          x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
+          for (int u = 0; u < 4; ++u) {
+            bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
+            x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if ((bal[u] >> lane) & 1u) atomicAdd(&h2[sub_bucket(x[u])], 1u);
+        }
+        __syncthreads();
+        // Sub-bucket starts (a contiguous range per thread) and the largest one.
+        const int per = (nb2 + RT - 1) / RT;
+        const int e0 = min(nb2, t * per), e1 = min(nb2, e0 + per);
+        int loc = 0, big = 0;
+        for (int e = e0; e < e1; ++e) {
+          loc += int(h2[e]);
+          big = max(big, int(h2[e]));
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if ((bal[u] >> lane) & 1u) {
-            const int bk = score_bucket(x[u]);
-            if (bk <= bstar) {
-              const uint32_t pos = atomicAdd(&hist[bk], 1u);
-              kbx[pos] = rank_key(x[u], uint32_t(int64_t(wd + u) * 32 + lane));
+        for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
+        if (lane == 0 && big > 0) atomicMax(&misc[3], big);
+        int run;
+        block_exscan(loc, tmp, run);  // its barriers also publish misc[3]
+        if (misc[3] <= A.bucket_cap) {
+          for (int e = e0; e < e1; ++e) {
+            const uint32_t v = h2[e];
+            h2[e] = uint32_t(run);
+            run += int(v);
+          }
+          __syncthreads();
+          for (int wd = w0; wd < w1; wd += 4) {
+            uint32_t bal[4], x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
+              x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if ((bal[u] >> lane) & 1u) {
+                const uint32_t pos = atomicAdd(&h2[sub_bucket(x[u])], 1u);
+                kbg[pos] = rank_key(x[u], uint32_t(int64_t(wd + u) * 32 + lane));
+              }
+            }
+          }
+          __syncthreads();  // h2[i] is now the end of sub-bucket i
+          for (int64_t p = t; p < cnt; p += RT) {
+            const uint64_t key = kbg[p];
+            const uint32_t x = ~uint32_t(key >> 32);
+            const int i2 = sub_bucket(x);
+            const int b0 = i2 ? int(h2[i2 - 1]) : 0, b1 = int(h2[i2]);
+            int r = 0;
+            for (int j = b0; j < b1; ++j) r += kbg[j] < key;
+            const int64_t pos = b0 + r;
+            A.out_idx[q * T + pos] = int32_t(uint32_t(key));
+            A.out_dist[q * T + pos] = 1.0f - __uint2float_rn(x) * kUnfix;
+          }
+          done = true;
+        }
+      }
+      __syncthreads();  // the bucket-key space and misc are free again
+    }
+    if (!done) {
+      const bool keys_smem = cnt <= A.sort_cap;
+      uint64_t* const kbx = keys_smem ? kb : kbg;
+      uint64_t* const ksx = keys_smem ? ks : ksg;
+      bool small = true;
+      {
+        // Bucket starts: exclusive scan of the histogram, four buckets per thread;
+        // the largest bucket up to bstar decides whether the counting step may run.
+        const bool whole = cut == cnt;  // every non-zero is returned: bstar is the last bucket
+        uint32_t c[NB / RT];
+        int part = 0, big = 0;
+  #pragma unroll
+        for (int k = 0; k < NB / RT; ++k) {
+          c[k] = hist[t * (NB / RT) + k];
+          part += int(c[k]);
+          big = max(big, int(c[k]));
+        }
+        if (whole) {
+  #pragma unroll
+          for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
+          if (lane == 0 && big > 0) atomicMax(&misc[1], big);
+        }
+        int base;
+        block_exscan(part, tmp, base);  // its barriers also publish misc[1]
+  #pragma unroll
+        for (int k = 0; k < NB / RT; ++k) {
+          hist[t * (NB / RT) + k] = uint32_t(base);
+          if (!whole && base <= cut - 1 && cut - 1 < base + int(c[k])) misc[2] = t * (NB / RT) + k;
+          base += int(c[k]);
+        }
+        __syncthreads();
+        if (whole) {
+          bstar = cnt > 0 ? NB - 1 : -1;
+        } else {
+          bstar = misc[2];
+          big = 0;
+  #pragma unroll
+          for (int k = 0; k < NB / RT; ++k)
+            if (t * (NB / RT) + k <= bstar) big = max(big, int(c[k]));
+  #pragma unroll
+          for (int o = 16; o > 0; o >>= 1) big = max(big, __shfl_xor_sync(kFull, big, o));
+          if (lane == 0 && big > 0) atomicMax(&misc[1], big);
+          __syncthreads();
+        }
+        small = misc[1] <= A.bucket_cap;
+      }
+      if (small) {
+        // Scatter the non-zeros of buckets 0 .. bstar to their bucket's range
+        // (any order inside it); afterwards hist[b] is the end of bucket b.
+        for (int wd = w0; wd < w1; wd += 4) {
+          uint32_t bal[4], x[4];
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
+            x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
+          }
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if ((bal[u] >> lane) & 1u) {
+              const int bk = score_bucket(x[u]);
+              if (bk <= bstar) {
+                const uint32_t pos = atomicAdd(&hist[bk], 1u);
+                kbx[pos] = rank_key(x[u], uint32_t(int64_t(wd + u) * 32 + lane));
+              }
             }
           }
         }
-      }
-      __syncthreads();
-      // Place of a key = its bucket's start + the number of smaller keys in
-      // the bucket (keys are distinct); the accumulator is no longer needed.
-      const int nsel = bstar >= 0 ? int(hist[bstar]) : 0;
-      for (int p = t; p < nsel; p += RT) {
-        const uint64_t key = kbx[p];
-        const int bk = score_bucket(~uint32_t(key >> 32));
-        const int b0 = bk ? int(hist[bk - 1]) : 0, b1 = int(hist[bk]);
-        int r = 0;
-        for (int j = b0; j < b1; ++j) r += kbx[j] < key;
-        ksx[b0 + r] = key;
-      }
-      __syncthreads();
-      const int64_t nout = tmin<int64_t>(T, cnt);
-      for (int64_t p = t; p < nout; p += RT) {
-        const uint64_t key = ksx[p];
-        A.out_idx[q * T + p] = int32_t(uint32_t(key));
-        A.out_dist[q * T + p] = 1.0f - __uint2float_rn(~uint32_t(key >> 32)) * kUnfix;
-      }
-    } else {
-      // Global-memory path: non-zeros compacted in gallery order, then the
-      // stable radix sort.
-      for (int wd = w0; wd < w1; wd += 4) {
-        uint32_t bal[4], x[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
-          x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
+        __syncthreads();
+        // Place of a key = its bucket's start + the number of smaller keys in
+        // the bucket (keys are distinct); the accumulator is no longer needed.
+        const int nsel = bstar >= 0 ? int(hist[bstar]) : 0;
+        for (int p = t; p < nsel; p += RT) {
+          const uint64_t key = kbx[p];
+          const int bk = score_bucket(~uint32_t(key >> 32));
+          const int b0 = bk ? int(hist[bk - 1]) : 0, b1 = int(hist[bk]);
+          int r = 0;
+          for (int j = b0; j < b1; ++j) r += kbx[j] < key;
+          ksx[b0 + r] = key;
         }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if ((bal[u] >> lane) & 1u) {
-            const int pos = off + __popc(bal[u] & lt);
-            gk0[pos] = ~x[u];
-            gv0[pos] = uint32_t(int64_t(wd + u) * 32 + lane);
+        __syncthreads();
+        const int64_t nout = tmin<int64_t>(T, cnt);
+        for (int64_t p = t; p < nout; p += RT) {
+          const uint64_t key = ksx[p];
+          A.out_idx[q * T + p] = int32_t(uint32_t(key));
+          A.out_dist[q * T + p] = 1.0f - __uint2float_rn(~uint32_t(key >> 32)) * kUnfix;
+        }
+      } else {
+        // Global-memory path: non-zeros compacted in gallery order, then the
+        // stable radix sort.
+        for (int wd = w0; wd < w1; wd += 4) {
+          uint32_t bal[4], x[4];
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            bal[u] = wd + u < w1 ? bits[wd + u] : 0u;
+            x[u] = ((bal[u] >> lane) & 1u) ? acc[int64_t(wd + u) * 32 + lane] : 0u;
           }
-          off += __popc(bal[u]);
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if ((bal[u] >> lane) & 1u) {
+              const int pos = off + __popc(bal[u] & lt);
+              gk0[pos] = ~x[u];
+              gv0[pos] = uint32_t(int64_t(wd + u) * 32 + lane);
+            }
+            off += __popc(bal[u]);
+          }
         }
-      }
-      __syncthreads();
-      uint32_t* k0 = gk0;
-      uint32_t* v0 = gv0;
-      uint32_t* k1 = gk1;
-      uint32_t* v1 = gv1;
-      block_radix_sort(k0, v0, k1, v1, cnt, hist, tmp, misc);
-      const int64_t nout = tmin<int64_t>(T, cnt);
-      for (int64_t p = t; p < nout; p += RT) {
-        const float s = __uint2float_rn(~k0[p]) * kUnfix;
-        A.out_idx[q * T + p] = int32_t(v0[p]);
-        A.out_dist[q * T + p] = 1.0f - s;
+        __syncthreads();
+        uint32_t* k0 = gk0;
+        uint32_t* v0 = gv0;
+        uint32_t* k1 = gk1;
+        uint32_t* v1 = gv1;
+        block_radix_sort(k0, v0, k1, v1, cnt, hist, tmp, misc);
+        const int64_t nout = tmin<int64_t>(T, cnt);
+        for (int64_t p = t; p < nout; p += RT) {
+          const float s = __uint2float_rn(~k0[p]) * kUnfix;
+          A.out_idx[q * T + p] = int32_t(v0[p]);
+          A.out_dist[q * T + p] = 1.0f - s;
+        }
       }
     }
     // The zero tail in gallery order.  Its distances are all 1: plain

@@ -226,7 +226,8 @@ def test_overflow_retry_path():
 def test_rank_sort_paths_agree():
     """The final ranking sorts each query's non-zero scores by buckets (for a
     truncated list only the buckets that reach it), with the keys in shared
-    memory or, beyond its cap, in global scratch; queries with too crowded a
+    memory or, beyond its cap, in global scratch, where full lists cut each
+    bucket into sub-buckets of about four keys; queries with too crowded a
     bucket take the global radix sort.  A test hook lowers both limits: every
     path gives the same lists, bit for bit, full or truncated, and they match
     the oracle."""
@@ -248,7 +249,7 @@ def test_rank_sort_paths_agree():
         "print('digest', hashlib.sha256(i.tobytes() + d.tobytes() + i2.tobytes() + d2.tobytes()).hexdigest())"
     )
     digests = []
-    for caps in (None, "0,256", "100,256", "8192,1", "8192,4"):
+    for caps in (None, "0,256", "100,256", "8192,1", "8192,4", "0,1", "0,4"):
         env = dict(os.environ)
         env.pop("RERANK_TEST_RANK_CAPS", None)
         if caps:
